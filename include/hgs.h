@@ -1,0 +1,235 @@
+/*
+ * hgs.h -- C ABI of the B300 (sm_103a) half-Gaussian splatting rasterizer.
+ *
+ * The library implements the differentiable tile rasterizer of 3D Half-Gaussian
+ * Splatting (3D-HGS, CVPR 2025): projection of each half-Gaussian pair to a 2D
+ * splat with SH colour, tile binning with a 64-bit (tile | depth) key radix
+ * sort, per-pixel front-to-back compositing of the pair weight of Eq. 10, and
+ * the matching backward pass.
+ *
+ * Conventions shared by every call
+ *  - Ownership: the caller allocates every buffer.  No call allocates or frees
+ *    memory (device or host), and none synchronises the host with the device.
+ *  - Pointers: unless a parameter says "host", it is a device pointer.  Float
+ *    arrays are FP32; any pointer read with vector loads (marked "16-B aligned")
+ *    must be 16-byte aligned.
+ *  - Streams: every call only enqueues work on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  The calls are stateless and thread-safe and
+ *    can be captured in a CUDA graph, provided the host arrays they read
+ *    (cams_host, cfg) keep the sizes used at capture time.
+ *  - Errors, two levels.  (1) The return value reports argument validation
+ *    (null pointers, sizes, unsupported options) and launch errors.  Nothing is
+ *    enqueued when it is not HGS_OK.  (2) `dev_status` is a device int that
+ *    kernels OR error bits into (HGS_DEV_*): pair capacity exceeded (the needed
+ *    count is still written to dev_num_pairs), a bounded spin-wait that timed
+ *    out, an index outside its array (the access is skipped).  The caller
+ *    zeroes it, reads it after the stream completes, and discards the outputs
+ *    of a step that set it.  A wait that times out never hangs the device.
+ *  - Layout of multi-view outputs: views are packed one after another.  View v
+ *    starts at pixel offset pix_off[v] = sum_{u<v} W_u H_u.  Images are
+ *    [3, H_v, W_v] planes at float offset 3*pix_off[v].  Per-pixel arrays are
+ *    [H_v, W_v] at offset pix_off[v].  Per-(view, splat) arrays are [n_views, n].
+ *    Global tile ids are tile_off[v] + ty*tiles_x(v) + tx, where
+ *    tile_off[v] = sum_{u<v} tiles_x(u) tiles_y(u).
+ */
+#ifndef HGS_H
+#define HGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HGS_VERSION 1
+#define HGS_MAX_VIEWS 256                 /* views per call                                     */
+#define HGS_MAX_PAIRS ((1u << 30) - 1u)   /* (tile, splat) pairs per call: 30-bit sort counters */
+#define HGS_MAX_SH_DEGREE 3
+
+typedef enum {
+    HGS_OK = 0,
+    HGS_ERR_INVALID = 1,      /* bad argument (null pointer, size, option)  */
+    HGS_ERR_CAPACITY = 2,     /* a caller buffer is too small               */
+    HGS_ERR_CUDA = 3,         /* a CUDA launch or runtime call failed       */
+    HGS_ERR_TIMEOUT = 4,      /* reserved for host-side waits (none today)  */
+    HGS_ERR_UNSUPPORTED = 5   /* option valid in principle but not built    */
+} hgs_status;
+
+/* bits OR-ed into *dev_status by kernels */
+#define HGS_DEV_CAPACITY 0x1  /* more (tile, splat) pairs than pair_capacity     */
+#define HGS_DEV_TIMEOUT 0x2   /* a look-back or queue spin hit its iteration cap */
+#define HGS_DEV_BOUNDS 0x4    /* an index was outside its array; access skipped  */
+
+/* Half-Gaussian parameters (Sec. 3.2), activated values, [n] rows:
+ *   means   [n,3]  world position mu
+ *   scales  [n,3]  standard deviations (> 0), the diagonal of S in Eq. 2
+ *   quats   [n,4]  rotation quaternion (w,x,y,z), any nonzero length
+ *   normals [n,3]  splitting-plane normal n, any length (0 => both halves weigh 1/2)
+ *   opac1   [n]    alpha_1, opacity of the half n.(x - mu) >= 0, in [0,1]
+ *   opac2   [n]    alpha_2, opacity of the other half, in [0,1]
+ *   sh      [n,(sh_degree+1)^2,3] real SH colour coefficients (16-B aligned)
+ * The real SH basis is sqrt2 Im Y_l^|m| (m<0), Y_l^0, sqrt2 Re Y_l^m (m>0) of the
+ * complex harmonics with the Condon-Shortley phase, index l*l + l + m; the
+ * colour is max(0, sum_lm c_lm Y_lm(dir) + 1/2), dir = unit(mu - camera centre). */
+typedef struct {
+    const float *means, *scales, *quats, *normals, *opac1, *opac2, *sh;
+    int n;
+    int sh_degree;
+} hgs_gaussians;
+
+/* Gradients, same shapes as hgs_gaussians (written, not accumulated). */
+typedef struct {
+    float *means, *scales, *quats, *normals, *opac1, *opac2, *sh;
+} hgs_gaussian_grads;
+
+/* Pinhole camera.  viewmat is world -> camera, row-major 3x4 [R | t]; pixel
+ * coordinates are u = fx x/z + cx, v = fy y/z + cy, and pixel (i, j) has its
+ * centre at (i + 1/2, j + 1/2).  Splats with camera z <= near_plane are culled.
+ * bg is the background colour composited behind the splats. */
+typedef struct {
+    float viewmat[12];
+    float fx, fy, cx, cy;
+    int width, height;
+    float near_plane;
+    float bg[3];
+} hgs_camera;
+
+/* Options.
+ *   tile_w, tile_h : 8x8, 16x16 or 32x8.  The tile shape changes the image
+ *                    (tiles are culled by the 3-sigma square, not per pixel).
+ *   batch          : splats staged in shared memory per round, 32..256,
+ *                    multiple of 32 (0 = tile_w*tile_h)
+ *   lowpass        : l added to the diagonal of hat Sigma (3D-GS uses 0.3)
+ *   fov_clamp      : 1 = clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS)
+ *   plain          : 1 = plain 3D-GS weight alpha1 * hat G (no half split)
+ *   persistent     : 1 = one persistent launch over a (view, tile) work queue,
+ *                    0 = one thread block per tile                            */
+typedef struct {
+    int tile_w, tile_h;
+    int batch;
+    float lowpass;
+    int fov_clamp;
+    int plain;
+    int persistent;
+} hgs_config;
+
+/* Per-(view, splat) projected records written by hgs_project, [n_views*n] rows.
+ *   rec    [.,12] (16-B aligned): mu_x, mu_y, conic A, B, C, w'_x, w'_y,
+ *                  alpha1, alpha2, r, g, b.  The conic is hat Sigma^-1 =
+ *                  [[A,B],[B,C]]; w' = hat Sigma^-1 k / sqrt(2 v), so that the
+ *                  half-plane fraction is P(d) = 1/2 erfc(-w'.d) (Eq. 8).
+ *   depth  [.]     camera-space z of the mean (the sort key's low 32 bits)
+ *   rect   [.,4]   (16-B aligned) covered tiles [x0,x1) x [y0,y1) of the view
+ *   tiles  [.]     number of covered tiles, 0 if culled                       */
+typedef struct {
+    float *rec;
+    float *depth;
+    int32_t *rect;
+    uint32_t *tiles;
+} hgs_proj;
+
+/* ---- sizes ------------------------------------------------------------- */
+
+/* Tiles and pixels of all views (host arrays).  Returns HGS_ERR_INVALID on a
+ * bad camera or option.  Any output pointer may be NULL. */
+hgs_status hgs_layout(const hgs_camera *cams_host, int n_views, const hgs_config *cfg,
+                      int *total_tiles, int64_t *total_pixels);
+
+/* Workspace bytes needed by hgs_bin for n splats, n_views views and room for
+ * pair_capacity (tile, splat) pairs. */
+size_t hgs_bin_workspace_size(int n, int n_views, size_t pair_capacity);
+
+/* Workspace bytes needed by hgs_render_fwd / hgs_rasterize_bwd / hgs_render_bwd. */
+size_t hgs_render_workspace_size(const hgs_camera *cams_host, int n_views, const hgs_config *cfg,
+                                 int n);
+
+/* ---- A1-A2: projection and SH colour ------------------------------------ */
+
+/* Projects every splat into every view: Sigma^w = R S S^T R^T (Eq. 2),
+ * hat Sigma = top-left 2x2 of J W Sigma^w W^T J^T (Eq. 3-5) plus the low-pass,
+ * its inverse (the conic), mu-hat, the 3-sigma tile rect and the half-plane
+ * terms of Eq. 7-8 (w'), and the SH colour.  Binning fields follow a fixed FP32
+ * operation order without fused multiply-adds.  Near-degenerate splats
+ * (ill-conditioned hat Sigma or a splitting plane nearly containing the ray)
+ * have their conic and half-plane terms recomputed in FP64.
+ * cams_host: host copy (sizes); cams_dev: the same cameras in device memory. */
+hgs_status hgs_project(const hgs_gaussians *g, const hgs_camera *cams_host,
+                       const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
+                       const hgs_proj *out, int *dev_status, void *stream);
+
+/* ---- A3-A5: binning ------------------------------------------------------ */
+
+/* Emits one (key, value) pair per covered tile of every (view, splat),
+ * key = (global tile id << 32) | bits of depth, value = view*n + splat, in
+ * (view, splat, row-major tile) order; sorts them with a stable LSD radix sort
+ * (8-bit digits, onesweep with bounded decoupled look-back) over the key bits in
+ * use, so that equal keys keep ascending value order; and writes per-tile
+ * [start, end) ranges (ranges[2*t], ranges[2*t+1]; [0,0) for an empty tile).
+ *   keys_out [pair_capacity] uint64, ids_out [pair_capacity] uint32,
+ *   ranges   [2*total_tiles] uint32, dev_num_pairs: uint64, the pair count.
+ * If the count exceeds pair_capacity, HGS_DEV_CAPACITY is set, the count is
+ * still written, and keys/ids/ranges are not meaningful. */
+hgs_status hgs_bin(const hgs_proj *proj, int n, const hgs_camera *cams_host, int n_views,
+                   const hgs_config *cfg, void *ws, size_t ws_bytes, size_t pair_capacity,
+                   uint64_t *keys_out, uint32_t *ids_out, uint32_t *ranges,
+                   uint64_t *dev_num_pairs, int *dev_status, void *stream);
+
+/* ---- A6: forward compositing ----------------------------------------------- */
+
+/* Per pixel, front to back over its tile's sorted list (Sec. 3.3 blending with
+ * the pair weight of Eq. 10):
+ *   a = min(0.99, (alpha2 + (alpha1 - alpha2) P(d)) exp(-d^T conic d / 2)),
+ * skip a < 1/255, stop before a splat that would take T below 1e-4.
+ *   image     [3*total_pixels] : C + T_final * bg, per view [3,H,W]
+ *   final_T   [total_pixels]   : T after the last composited splat
+ *   n_contrib [total_pixels]   : 1 + position (in the tile's list) of the last
+ *                                composited splat, 0 if none               */
+hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
+                          const uint32_t *ranges, const hgs_camera *cams_host,
+                          const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
+                          void *ws, size_t ws_bytes, float *image, float *final_T,
+                          uint32_t *n_contrib, int *dev_status, void *stream);
+
+/* ---- A7: backward compositing ---------------------------------------------- */
+
+/* Adjoint of hgs_render_fwd for the upstream gradient dL_dimage (layout of
+ * image).  Per pixel, back to front from n_contrib, the transmittance is
+ * rebuilt by division (T_i = T_{i+1} / (1 - a_i)).  It writes the screen-space
+ * gradient of every (view, splat):
+ *   grad2d [n_views*n, 12] (16-B aligned): d mu_x, d mu_y, d A, d B, d C,
+ *          d w'_x, d w'_y, d alpha1, d alpha2, d r, d g, d b.
+ * The call zeroes grad2d first.  Gradients through the 0.99 clamp, through
+ * skipped or terminated splats and through P of a degenerate plane are 0. */
+hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids,
+                             const uint32_t *ranges, const hgs_camera *cams_host,
+                             const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
+                             void *ws, size_t ws_bytes, const float *final_T,
+                             const uint32_t *n_contrib, const float *dL_dimage,
+                             float *grad2d, int *dev_status, void *stream);
+
+/* ---- A8: projection backward ------------------------------------------------ */
+
+/* Chain rule from grad2d through Eq. 8, Eq. 3-5, Eq. 2 and the SH colour to
+ * every parameter, summed over views.  Writes every entry of `out`. */
+hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host,
+                           const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
+                           const float *grad2d, const hgs_gaussian_grads *out,
+                           int *dev_status, void *stream);
+
+/* hgs_rasterize_bwd followed by hgs_project_bwd; grad2d is caller scratch. */
+hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const uint32_t *ids,
+                          const uint32_t *ranges, const hgs_camera *cams_host,
+                          const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
+                          void *ws, size_t ws_bytes, const float *final_T,
+                          const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                          const hgs_gaussian_grads *out, int *dev_status, void *stream);
+
+/* ---- misc ------------------------------------------------------------------- */
+const char *hgs_status_string(hgs_status s);
+int hgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGS_H */

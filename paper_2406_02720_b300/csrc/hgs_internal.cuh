@@ -1,0 +1,127 @@
+// Internal declarations shared by the CUDA sources of libhgs (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hgs.h"
+
+namespace hgs {
+
+constexpr int kMaxViews = HGS_MAX_VIEWS;
+
+// Host-computed per-view offsets, passed to kernels by value (4 KB; kernels may
+// take up to 32 KB of parameters on sm_70 and later).
+struct ViewTable {
+    int n_views;
+    int total_tiles;
+    int tile_off[kMaxViews + 1];       // global tile id offset of each view
+    int tiles_x[kMaxViews];            // tiles per row of each view
+    long long pix_off[kMaxViews + 1];  // pixel offset of each view
+};
+
+// Which view a global tile id belongs to (binary search over tile_off).
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, int gtile) {
+    int lo = 0, hi = vt.n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (vt.tile_off[mid] <= gtile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__host__ __device__ __forceinline__ int div_up(int a, int b) { return (a + b - 1) / b; }
+
+// Bounded spin-waits: the cap, and how long a waiting thread backs off.
+constexpr unsigned kSpinCap = 1u << 22;
+constexpr unsigned kSpinSleepNs = 64;
+
+__device__ __forceinline__ void set_status(int *st, int bit) {
+    if (st) atomicOr(st, bit);
+}
+
+// Relaxed device-scope 32/64-bit load and store (look-back words; L1 bypassed).
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Host-side launchers (one per kernel family), defined in the .cu files.
+struct ProjLaunch {
+    hgs_gaussians g;
+    const hgs_camera *cams;
+    int n_views;
+    hgs_config cfg;
+    hgs_proj out;
+    ViewTable vt;
+    int *status;
+};
+cudaError_t launch_project(const ProjLaunch &p, cudaStream_t s);
+
+struct ProjBwdLaunch {
+    hgs_gaussians g;
+    const hgs_camera *cams;
+    int n_views;
+    hgs_config cfg;
+    const float *grad2d;
+    hgs_gaussian_grads out;
+    int *status;
+};
+cudaError_t launch_project_bwd(const ProjBwdLaunch &p, cudaStream_t s);
+
+// Binning workspace carve-up (see binning.cu).
+struct BinLaunch {
+    const hgs_proj *proj;
+    int n, n_views;
+    ViewTable vt;
+    hgs_config cfg;
+    void *ws;
+    size_t ws_bytes;
+    size_t capacity;
+    uint64_t *keys_out;
+    uint32_t *ids_out;
+    uint32_t *ranges;
+    uint64_t *num_pairs;
+    int *status;
+};
+size_t bin_workspace_bytes(int n, int n_views, size_t capacity);
+cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s);
+
+struct RenderLaunch {
+    hgs_proj proj;
+    int n;
+    const uint32_t *ids;
+    const uint32_t *ranges;
+    const hgs_camera *cams;
+    ViewTable vt;
+    hgs_config cfg;
+    void *ws;
+    size_t ws_bytes;
+    // forward outputs / backward inputs
+    float *image;
+    float *final_T;
+    uint32_t *n_contrib;
+    // backward
+    const float *dL_dimage;
+    float *grad2d;
+    int *status;
+};
+size_t render_workspace_bytes(const ViewTable &vt, const hgs_config &cfg);
+cudaError_t launch_render_fwd(const RenderLaunch &p, cudaStream_t s);
+cudaError_t launch_render_bwd(const RenderLaunch &p, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace hgs

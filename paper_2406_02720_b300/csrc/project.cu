@@ -1,0 +1,662 @@
+// Projection of half-Gaussian pairs to screen-space splats (A1 + A2) and its
+// adjoint (A8).
+//
+// Forward, per (splat, view):
+//   Eq. 2      Sigma^w = R S S^T R^T, factored as L L^T with L = R diag(s)
+//   Eq. 3-5    hat Sigma = P P^T + l I with P = M L, M = J W (2x3): the top-left
+//              2x2 block of J W Sigma^w W^T J^T, plus the 3D-GS low-pass l
+//   Eq. 7-8    half-plane fraction P(d) = Pr[n.(x-mu) >= 0 | pixel offset d]
+//              = 1/2 erfc(-w'.d) with u = L^T n^, var_s = |u|^2, k = P u,
+//              w = hat Sigma^-1 k, v = var_s - k.w, w' = w / sqrt(2 v)
+//   Sec. 3.1   view-dependent SH colour
+// The binning fields (depth, mu-hat, hat Sigma, 3-sigma radius, tile rect) use a
+// fixed FP32 operation order with no fused multiply-add (__f*_rn intrinsics), so
+// that the integer decisions they feed are reproducible.  The continuous terms
+// are FP32; splats whose hat Sigma is ill-conditioned or whose plane nearly
+// contains the ray get their conic and half-plane terms recomputed in FP64.
+#include <math.h>
+
+#include "hgs_internal.cuh"
+
+namespace hgs {
+namespace {
+
+constexpr int kProjBlock = 256;
+enum { MODE_CULLED = 0, MODE_NORMAL = 1, MODE_STEP = 2, MODE_HALF = 3 };
+
+// Degeneracy tests that send a splat to the FP64 path.
+constexpr float kDetRelFp64 = 1e-4f;   // det < kDetRelFp64 * a * c
+constexpr float kVRelFp64 = 1e-3f;     // v   < kVRelFp64 * var_s
+// Scale applied to w in step mode (v ~ 0): P becomes a step at w.d = 0.
+constexpr float kStepScale = 1.2089258196146292e24f;   // 2^80
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+
+struct Canon {
+    bool culled;
+    float depth, mux, muy, a, b, c, det;
+    float L[3][3];
+    float P[2][3];
+    int rect[4];
+    unsigned tiles;
+};
+
+// Binning fields in the fixed FP32 order (one IEEE op per step).
+__device__ __forceinline__ void canon_project(const float m[3], const float s[3], const float q[4],
+                                              const hgs_camera &cam, float lp, int fov_clamp,
+                                              int tw, int th, Canon &o) {
+    o.culled = true;
+    o.tiles = 0;
+    o.rect[0] = o.rect[1] = o.rect[2] = o.rect[3] = 0;
+    const float *V = cam.viewmat;
+    // 1. unit quaternion
+    float n2 = fm(q[0], q[0]);
+    n2 = fa(n2, fm(q[1], q[1]));
+    n2 = fa(n2, fm(q[2], q[2]));
+    n2 = fa(n2, fm(q[3], q[3]));
+    float qn = __fsqrt_rn(n2);
+    float w = fdv(q[0], qn), x = fdv(q[1], qn), y = fdv(q[2], qn), z = fdv(q[3], qn);
+    // 2. rotation
+    float R[3][3];
+    R[0][0] = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
+    R[0][1] = fm(2.0f, fs(fm(x, y), fm(w, z)));
+    R[0][2] = fm(2.0f, fa(fm(x, z), fm(w, y)));
+    R[1][0] = fm(2.0f, fa(fm(x, y), fm(w, z)));
+    R[1][1] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
+    R[1][2] = fm(2.0f, fs(fm(y, z), fm(w, x)));
+    R[2][0] = fm(2.0f, fs(fm(x, z), fm(w, y)));
+    R[2][1] = fm(2.0f, fa(fm(y, z), fm(w, x)));
+    R[2][2] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
+    // 3. L = R diag(s)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o.L[i][k] = fm(R[i][k], s[k]);
+    // 4. camera-space mean
+    float t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float acc = fm(V[4 * i + 0], m[0]);
+        acc = fa(acc, fm(V[4 * i + 1], m[1]));
+        acc = fa(acc, fm(V[4 * i + 2], m[2]));
+        t[i] = fa(acc, V[4 * i + 3]);
+    }
+    o.depth = t[2];
+    // 5. near-plane cull
+    if (!(t[2] > cam.near_plane)) return;
+    // 6. clamped x/z, y/z
+    float ux = fdv(t[0], t[2]), uy = fdv(t[1], t[2]);
+    float uxc = ux, uyc = uy;
+    if (fov_clamp) {
+        float limx = fm(1.3f, fdv(fm(0.5f, (float)cam.width), cam.fx));
+        float limy = fm(1.3f, fdv(fm(0.5f, (float)cam.height), cam.fy));
+        uxc = fminf(fmaxf(ux, -limx), limx);
+        uyc = fminf(fmaxf(uy, -limy), limy);
+    }
+    // 7. Jacobian
+    float j00 = fdv(cam.fx, t[2]);
+    float j02 = -fdv(fm(cam.fx, uxc), t[2]);
+    float j11 = fdv(cam.fy, t[2]);
+    float j12 = -fdv(fm(cam.fy, uyc), t[2]);
+    // 8. M = J W
+    float M[2][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        M[0][k] = fa(fm(j00, V[k]), fm(j02, V[8 + k]));
+        M[1][k] = fa(fm(j11, V[4 + k]), fm(j12, V[8 + k]));
+    }
+    // 9. P = M L
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = fm(M[i][0], o.L[0][k]);
+            acc = fa(acc, fm(M[i][1], o.L[1][k]));
+            o.P[i][k] = fa(acc, fm(M[i][2], o.L[2][k]));
+        }
+    // 10. hat Sigma
+    float a = fm(o.P[0][0], o.P[0][0]);
+    a = fa(a, fm(o.P[0][1], o.P[0][1]));
+    a = fa(a, fm(o.P[0][2], o.P[0][2]));
+    a = fa(a, lp);
+    float b = fm(o.P[0][0], o.P[1][0]);
+    b = fa(b, fm(o.P[0][1], o.P[1][1]));
+    b = fa(b, fm(o.P[0][2], o.P[1][2]));
+    float c = fm(o.P[1][0], o.P[1][0]);
+    c = fa(c, fm(o.P[1][1], o.P[1][1]));
+    c = fa(c, fm(o.P[1][2], o.P[1][2]));
+    c = fa(c, lp);
+    o.a = a; o.b = b; o.c = c;
+    // 11. determinant cull
+    float det = fs(fm(a, c), fm(b, b));
+    o.det = det;
+    if (!(det > 0.0f)) return;
+    // 12. radius
+    float mid = fm(0.5f, fa(a, c));
+    float lam = fa(mid, __fsqrt_rn(fmaxf(0.1f, fs(fm(mid, mid), det))));
+    float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
+    // 13. centre
+    float mux = fa(fm(cam.fx, fdv(t[0], t[2])), cam.cx);
+    float muy = fa(fm(cam.fy, fdv(t[1], t[2])), cam.cy);
+    o.mux = mux; o.muy = muy;
+    // 14. finiteness
+    if (!(isfinite(mux) && isfinite(muy) && isfinite(r))) return;
+    // 15. tile rect
+    int tiles_x = div_up(cam.width, tw), tiles_y = div_up(cam.height, th);
+    float ftw = (float)tw, fth = (float)th;
+    float x0 = floorf(fdv(fs(mux, r), ftw));
+    float x1 = fa(floorf(fdv(fa(mux, r), ftw)), 1.0f);
+    float y0 = floorf(fdv(fs(muy, r), fth));
+    float y1 = fa(floorf(fdv(fa(muy, r), fth)), 1.0f);
+    x0 = fminf(fmaxf(x0, 0.0f), (float)tiles_x);
+    x1 = fminf(fmaxf(x1, 0.0f), (float)tiles_x);
+    y0 = fminf(fmaxf(y0, 0.0f), (float)tiles_y);
+    y1 = fminf(fmaxf(y1, 0.0f), (float)tiles_y);
+    o.rect[0] = (int)x0; o.rect[1] = (int)y0; o.rect[2] = (int)x1; o.rect[3] = (int)y1;
+    int nx = o.rect[2] - o.rect[0], ny = o.rect[3] - o.rect[1];
+    o.tiles = (nx > 0 && ny > 0) ? (unsigned)(nx * ny) : 0u;
+    o.culled = false;
+}
+
+// Full projection in precision T (FP64 fallback; FP32/FP64 recompute in the
+// backward).  Same mathematics as canon_project plus the half-plane terms, with
+// free operation order.
+template <typename T>
+struct Proj {
+    T qn, qh[4], R[3][3], L[3][3], t[3], uxc, uyc;
+    bool clx, cly;
+    T J00, J02, J11, J12, M[2][3], P[2][3], a, b, c, det, Q[3];
+    T nn, nh[3], u[3], var_s, k[2], w[2], v;
+    int mode;
+
+    __device__ __forceinline__ void run(const float *m, const float *s, const float *q,
+                                        const float *nrm, const hgs_camera &cam, float lp,
+                                        int fov_clamp) {
+        const float *V = cam.viewmat;
+        qn = sqrt((T)q[0] * q[0] + (T)q[1] * q[1] + (T)q[2] * q[2] + (T)q[3] * q[3]);
+        T iq = (T)1 / qn;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) qh[i] = (T)q[i] * iq;
+        const T a0 = qh[0], a1 = qh[1], a2 = qh[2], a3 = qh[3];   // (w, x, y, z)
+        R[0][0] = 1 - 2 * (a2 * a2 + a3 * a3); R[0][1] = 2 * (a1 * a2 - a0 * a3); R[0][2] = 2 * (a1 * a3 + a0 * a2);
+        R[1][0] = 2 * (a1 * a2 + a0 * a3); R[1][1] = 1 - 2 * (a1 * a1 + a3 * a3); R[1][2] = 2 * (a2 * a3 - a0 * a1);
+        R[2][0] = 2 * (a1 * a3 - a0 * a2); R[2][1] = 2 * (a2 * a3 + a0 * a1); R[2][2] = 1 - 2 * (a1 * a1 + a2 * a2);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) L[i][kk] = R[i][kk] * (T)s[kk];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            t[i] = (T)V[4 * i] * m[0] + (T)V[4 * i + 1] * m[1] + (T)V[4 * i + 2] * m[2] + (T)V[4 * i + 3];
+        T ux = t[0] / t[2], uy = t[1] / t[2];
+        uxc = ux; uyc = uy; clx = cly = false;
+        if (fov_clamp) {
+            T limx = (T)1.3 * ((T)0.5 * cam.width / (T)cam.fx);
+            T limy = (T)1.3 * ((T)0.5 * cam.height / (T)cam.fy);
+            if (ux > limx) { uxc = limx; clx = true; }
+            if (ux < -limx) { uxc = -limx; clx = true; }
+            if (uy > limy) { uyc = limy; cly = true; }
+            if (uy < -limy) { uyc = -limy; cly = true; }
+        }
+        J00 = (T)cam.fx / t[2]; J02 = -(T)cam.fx * uxc / t[2];
+        J11 = (T)cam.fy / t[2]; J12 = -(T)cam.fy * uyc / t[2];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            M[0][kk] = J00 * V[kk] + J02 * V[8 + kk];
+            M[1][kk] = J11 * V[4 + kk] + J12 * V[8 + kk];
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) P[i][kk] = M[i][0] * L[0][kk] + M[i][1] * L[1][kk] + M[i][2] * L[2][kk];
+        a = P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2] + (T)lp;
+        b = P[0][0] * P[1][0] + P[0][1] * P[1][1] + P[0][2] * P[1][2];
+        c = P[1][0] * P[1][0] + P[1][1] * P[1][1] + P[1][2] * P[1][2] + (T)lp;
+        det = a * c - b * b;
+        T id = (T)1 / det;
+        Q[0] = c * id; Q[1] = -b * id; Q[2] = a * id;
+        nn = sqrt((T)nrm[0] * nrm[0] + (T)nrm[1] * nrm[1] + (T)nrm[2] * nrm[2]);
+        var_s = v = 0; k[0] = k[1] = w[0] = w[1] = 0;
+        u[0] = u[1] = u[2] = nh[0] = nh[1] = nh[2] = 0;
+        if (nn < (T)1e-12) { mode = MODE_HALF; return; }
+        T in = (T)1 / nn;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) nh[i] = (T)nrm[i] * in;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) u[kk] = L[0][kk] * nh[0] + L[1][kk] * nh[1] + L[2][kk] * nh[2];
+        var_s = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        k[0] = P[0][0] * u[0] + P[0][1] * u[1] + P[0][2] * u[2];
+        k[1] = P[1][0] * u[0] + P[1][1] * u[1] + P[1][2] * u[2];
+        w[0] = Q[0] * k[0] + Q[1] * k[1];
+        w[1] = Q[1] * k[0] + Q[2] * k[1];
+        v = var_s - (k[0] * w[0] + k[1] * w[1]);
+        mode = (v <= (T)1e-12 * var_s) ? MODE_STEP : MODE_NORMAL;
+    }
+
+    __device__ __forceinline__ bool degenerate() const {
+        return det < (T)kDetRelFp64 * a * c || (mode == MODE_NORMAL && v < (T)kVRelFp64 * var_s);
+    }
+};
+
+// ---- real spherical harmonics, degree <= 3 ---------------------------------
+// Basis (Condon-Shortley phase, index l*l + l + m):
+//   l=0: 1/(2 sqrt(pi))
+//   l=1: -c1 y, c1 z, -c1 x                          c1 = sqrt(3/(4 pi))
+//   l=2: c2a xy, -c2a yz, c2b (2z^2-x^2-y^2), -c2a xz, c2c (x^2-y^2)
+//        c2a = sqrt(15/pi)/2, c2b = sqrt(5/pi)/4, c2c = sqrt(15/pi)/4
+//   l=3: -c3a y(3x^2-y^2), c3b xyz, -c3c y(4z^2-x^2-y^2), c3d z(2z^2-3x^2-3y^2),
+//        -c3c x(4z^2-x^2-y^2), c3e z(x^2-y^2), -c3a x(x^2-3y^2)
+//        c3a = sqrt(70/pi)/8, c3b = sqrt(105/pi)/2, c3c = sqrt(42/pi)/8,
+//        c3d = sqrt(7/pi)/4, c3e = sqrt(105/pi)/4
+constexpr float kC0 = 0.28209479177387814f;
+constexpr float kC1 = 0.48860251190291992f;
+constexpr float kC2a = 1.0925484305920792f;
+constexpr float kC2b = 0.31539156525252005f;
+constexpr float kC2c = 0.54627421529603959f;
+constexpr float kC3a = 0.59004358992664352f;
+constexpr float kC3b = 2.8906114426405538f;
+constexpr float kC3c = 0.45704579946446572f;
+constexpr float kC3d = 0.37317633259011540f;
+constexpr float kC3e = 1.4453057213202769f;
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
+    Y[0] = kC0;
+    if (deg < 1) return;
+    Y[1] = -kC1 * y; Y[2] = kC1 * z; Y[3] = -kC1 * x;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kC2a * x * y;
+    Y[5] = -kC2a * y * z;
+    Y[6] = kC2b * (2.0f * zz - xx - yy);
+    Y[7] = -kC2a * x * z;
+    Y[8] = kC2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -kC3a * y * (3.0f * xx - yy);
+    Y[10] = kC3b * x * y * z;
+    Y[11] = -kC3c * y * (4.0f * zz - xx - yy);
+    Y[12] = kC3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -kC3c * x * (4.0f * zz - xx - yy);
+    Y[14] = kC3e * z * (xx - yy);
+    Y[15] = -kC3a * x * (xx - 3.0f * yy);
+}
+
+// Cartesian gradient of each basis polynomial.
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float dY[16][3]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dY[i][0] = dY[i][1] = dY[i][2] = 0.0f;
+    if (deg < 1) return;
+    dY[1][1] = -kC1; dY[2][2] = kC1; dY[3][0] = -kC1;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    dY[4][0] = kC2a * y; dY[4][1] = kC2a * x;
+    dY[5][1] = -kC2a * z; dY[5][2] = -kC2a * y;
+    dY[6][0] = -2.0f * kC2b * x; dY[6][1] = -2.0f * kC2b * y; dY[6][2] = 4.0f * kC2b * z;
+    dY[7][0] = -kC2a * z; dY[7][2] = -kC2a * x;
+    dY[8][0] = 2.0f * kC2c * x; dY[8][1] = -2.0f * kC2c * y;
+    if (deg < 3) return;
+    dY[9][0] = -kC3a * 6.0f * x * y; dY[9][1] = -kC3a * 3.0f * (xx - yy);
+    dY[10][0] = kC3b * y * z; dY[10][1] = kC3b * x * z; dY[10][2] = kC3b * x * y;
+    dY[11][0] = 2.0f * kC3c * x * y; dY[11][1] = -kC3c * (4.0f * zz - xx - 3.0f * yy);
+    dY[11][2] = -8.0f * kC3c * y * z;
+    dY[12][0] = -6.0f * kC3d * x * z; dY[12][1] = -6.0f * kC3d * y * z;
+    dY[12][2] = kC3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    dY[13][0] = -kC3c * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * kC3c * x * y;
+    dY[13][2] = -8.0f * kC3c * x * z;
+    dY[14][0] = 2.0f * kC3e * x * z; dY[14][1] = -2.0f * kC3e * y * z; dY[14][2] = kC3e * (xx - yy);
+    dY[15][0] = -3.0f * kC3a * (xx - yy); dY[15][1] = 6.0f * kC3a * x * y;
+}
+
+__device__ __forceinline__ void camera_centre(const hgs_camera &cam, float c[3]) {
+    const float *V = cam.viewmat;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] = -(V[i] * V[3] + V[4 + i] * V[7] + V[8 + i] * V[11]);
+}
+
+// Coalesced float4 staging of a [n,3] array slice into shared memory.
+__device__ __forceinline__ void stage3(const float *__restrict__ src, int n, int base, float *dst) {
+    int cnt = 3 * min(kProjBlock, n - base);
+    const float *s = src + 3 * (size_t)base;
+    int n4 = cnt >> 2;
+    for (int j = threadIdx.x; j < n4; j += blockDim.x)
+        reinterpret_cast<float4 *>(dst)[j] = __ldg(reinterpret_cast<const float4 *>(s) + j);
+    for (int j = 4 * n4 + threadIdx.x; j < cnt; j += blockDim.x) dst[j] = __ldg(s + j);
+}
+
+__global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
+    __shared__ __align__(16) float s_mean[3 * kProjBlock];
+    __shared__ __align__(16) float s_scale[3 * kProjBlock];
+    __shared__ __align__(16) float s_nrm[3 * kProjBlock];
+    const int n = p.g.n;
+    const int base = blockIdx.x * kProjBlock;
+    stage3(p.g.means, n, base, s_mean);
+    stage3(p.g.scales, n, base, s_scale);
+    stage3(p.g.normals, n, base, s_nrm);
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    if (i >= n) return;
+    float m[3], s[3], nrm[3], q[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m[k] = s_mean[3 * threadIdx.x + k];
+        s[k] = s_scale[3 * threadIdx.x + k];
+        nrm[k] = s_nrm[3 * threadIdx.x + k];
+    }
+    float4 q4 = __ldg(reinterpret_cast<const float4 *>(p.g.quats) + i);
+    q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
+    const float o1 = __ldg(p.g.opac1 + i), o2 = __ldg(p.g.opac2 + i);
+    const int deg = p.g.sh_degree;
+    const int nc = (deg + 1) * (deg + 1);
+    float sh[48];
+    bool sh_loaded = false;
+    const float lp = p.cfg.lowpass;
+
+    for (int v = 0; v < p.n_views; ++v) {
+        const hgs_camera &cam = p.cams[v];
+        const size_t vi = (size_t)v * n + i;
+        Canon cb;
+        canon_project(m, s, q, cam, lp, p.cfg.fov_clamp, p.cfg.tile_w, p.cfg.tile_h, cb);
+        p.out.depth[vi] = cb.depth;
+        reinterpret_cast<int4 *>(p.out.rect)[vi] = make_int4(cb.rect[0], cb.rect[1], cb.rect[2], cb.rect[3]);
+        p.out.tiles[vi] = cb.culled ? 0u : cb.tiles;
+        if (cb.culled || cb.tiles == 0) continue;
+
+        // conic and half-plane terms, FP32
+        float id = 1.0f / cb.det;
+        float Q0 = cb.c * id, Q1 = -cb.b * id, Q2 = cb.a * id;
+        float wpx = 0.0f, wpy = 0.0f;
+        float nn = sqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        int mode = MODE_HALF;
+        float wx = 0, wy = 0, vv = 0, var_s = 0;
+        if (nn >= 1e-12f) {
+            float in = 1.0f / nn;
+            float nh[3] = {nrm[0] * in, nrm[1] * in, nrm[2] * in};
+            float u[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) u[k] = cb.L[0][k] * nh[0] + cb.L[1][k] * nh[1] + cb.L[2][k] * nh[2];
+            var_s = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            float k0 = cb.P[0][0] * u[0] + cb.P[0][1] * u[1] + cb.P[0][2] * u[2];
+            float k1 = cb.P[1][0] * u[0] + cb.P[1][1] * u[1] + cb.P[1][2] * u[2];
+            wx = Q0 * k0 + Q1 * k1;
+            wy = Q1 * k0 + Q2 * k1;
+            vv = var_s - (k0 * wx + k1 * wy);
+            mode = (vv <= 1e-12f * var_s) ? MODE_STEP : MODE_NORMAL;
+        }
+        bool degen = cb.det < kDetRelFp64 * cb.a * cb.c || (nn >= 1e-12f && vv < kVRelFp64 * var_s);
+        if (degen) {
+            Proj<double> d;
+            d.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
+            if (d.det > 0.0) {
+                Q0 = (float)d.Q[0]; Q1 = (float)d.Q[1]; Q2 = (float)d.Q[2];
+            }
+            mode = d.mode;
+            if (mode == MODE_NORMAL) {
+                double sc = 1.0 / sqrt(2.0 * d.v);
+                wpx = (float)(d.w[0] * sc); wpy = (float)(d.w[1] * sc);
+            } else if (mode == MODE_STEP) {
+                wpx = (float)d.w[0] * kStepScale; wpy = (float)d.w[1] * kStepScale;
+            }
+        } else if (mode == MODE_NORMAL) {
+            float sc = rsqrtf(2.0f * vv);
+            wpx = wx * sc; wpy = wy * sc;
+        } else if (mode == MODE_STEP) {
+            wpx = wx * kStepScale; wpy = wy * kStepScale;
+        }
+
+        // SH colour
+        if (!sh_loaded) {
+            const float4 *sp = reinterpret_cast<const float4 *>(p.g.sh + (size_t)i * nc * 3);
+            int n4 = (nc * 3) >> 2;
+            if (((nc * 3) & 3) == 0 && ((reinterpret_cast<uintptr_t>(sp) & 15) == 0)) {
+#pragma unroll
+                for (int j = 0; j < 12; ++j)
+                    if (j < n4) {
+                        float4 t4 = __ldg(sp + j);
+                        sh[4 * j] = t4.x; sh[4 * j + 1] = t4.y; sh[4 * j + 2] = t4.z; sh[4 * j + 3] = t4.w;
+                    }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 48; ++j)
+                    if (j < nc * 3) sh[j] = __ldg(p.g.sh + (size_t)i * nc * 3 + j);
+            }
+            sh_loaded = true;
+        }
+        float cpos[3];
+        camera_centre(cam, cpos);
+        float dx = m[0] - cpos[0], dy = m[1] - cpos[1], dz = m[2] - cpos[2];
+        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis(deg, dx * il, dy * il, dz * il, Y);
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < 16; ++l)
+                if (l < nc) acc += sh[3 * l + ch] * Y[l];
+            rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
+        }
+        float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 3 * vi;
+        rec[0] = make_float4(cb.mux, cb.muy, Q0, Q1);
+        rec[1] = make_float4(Q2, wpx, wpy, o1);
+        rec[2] = make_float4(o2, rgb[0], rgb[1], rgb[2]);
+    }
+}
+
+// ---- adjoint -------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const hgs_camera &cam,
+                                         const float *g2, float gm[3], float gs[3], float gq[4],
+                                         float gn[3]) {
+    const float *V = cam.viewmat;
+    T gA = g2[2], gB = g2[3], gC = g2[4];
+    T gk[2] = {0, 0}, gvar = 0;
+    if (f.mode == MODE_NORMAL) {
+        T sv = (T)1 / sqrt((T)2 * f.v);
+        T gw0 = (T)g2[5] * sv, gw1 = (T)g2[6] * sv;
+        T gv = -((T)g2[5] * f.w[0] + (T)g2[6] * f.w[1]) * sv * sv * sv;
+        gvar = gv;
+        gk[0] = -gv * f.w[0]; gk[1] = -gv * f.w[1];
+        gw0 -= gv * f.k[0]; gw1 -= gv * f.k[1];
+        gA += gw0 * f.k[0]; gB += gw0 * f.k[1] + gw1 * f.k[0]; gC += gw1 * f.k[1];
+        gk[0] += f.Q[0] * gw0 + f.Q[1] * gw1;
+        gk[1] += f.Q[1] * gw0 + f.Q[2] * gw1;
+    }
+    // hat Sigma from the conic: Gs = -Q [[gA, gB/2], [gB/2, gC]] Q
+    T hb = (T)0.5 * gB;
+    T X00 = f.Q[0] * gA + f.Q[1] * hb, X01 = f.Q[0] * hb + f.Q[1] * gC;
+    T X10 = f.Q[1] * gA + f.Q[2] * hb, X11 = f.Q[1] * hb + f.Q[2] * gC;
+    T Gs00 = -(X00 * f.Q[0] + X01 * f.Q[1]);
+    T Gs01 = -(X00 * f.Q[1] + X01 * f.Q[2]);
+    T Gs11 = -(X10 * f.Q[1] + X11 * f.Q[2]);
+    // hat Sigma = P P^T + l I and k = P u
+    T gP[2][3], gu[3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        gP[0][kk] = 2 * (Gs00 * f.P[0][kk] + Gs01 * f.P[1][kk]) + gk[0] * f.u[kk];
+        gP[1][kk] = 2 * (Gs01 * f.P[0][kk] + Gs11 * f.P[1][kk]) + gk[1] * f.u[kk];
+        gu[kk] = f.P[0][kk] * gk[0] + f.P[1][kk] * gk[1] + 2 * gvar * f.u[kk];
+    }
+    // P = M L
+    T gM[2][3], gL[3][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gM[i][j] = gP[i][0] * f.L[j][0] + gP[i][1] * f.L[j][1] + gP[i][2] * f.L[j][2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) gL[j][kk] = f.M[0][j] * gP[0][kk] + f.M[1][j] * gP[1][kk] + f.nh[j] * gu[kk];
+    // u = L^T n^, n^ = n / |n|
+    if (f.mode != MODE_HALF) {
+        T gnh[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gnh[j] = f.L[j][0] * gu[0] + f.L[j][1] * gu[1] + f.L[j][2] * gu[2];
+        T dd = gnh[0] * f.nh[0] + gnh[1] * f.nh[1] + gnh[2] * f.nh[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gn[j] += (float)((gnh[j] - dd * f.nh[j]) / f.nn);
+    }
+    // L = R diag(s)
+    T gR[3][3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gR[j][kk] = gL[j][kk] * (T)s[kk];
+            acc += gL[j][kk] * f.R[j][kk];
+        }
+        gs[kk] += (float)acc;
+    }
+    // R(q^), q^ = q / |q|
+    T w = f.qh[0], x = f.qh[1], y = f.qh[2], z = f.qh[3];
+    T gqh[4];
+    gqh[0] = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+    gqh[1] = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] - w * gR[1][2] + z * gR[2][0] +
+                  w * gR[2][1] - 2 * x * gR[2][2]);
+    gqh[2] = 2 * (-2 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] - w * gR[2][0] +
+                  z * gR[2][1] - 2 * y * gR[2][2]);
+    gqh[3] = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2 * z * gR[1][1] + y * gR[1][2] +
+                  x * gR[2][0] + y * gR[2][1]);
+    T dq = gqh[0] * w + gqh[1] * x + gqh[2] * y + gqh[3] * z;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gq[j] += (float)((gqh[j] - dq * f.qh[j]) / f.qn);
+    // M = J W
+    T gJ00 = gM[0][0] * V[0] + gM[0][1] * V[1] + gM[0][2] * V[2];
+    T gJ02 = gM[0][0] * V[8] + gM[0][1] * V[9] + gM[0][2] * V[10];
+    T gJ11 = gM[1][0] * V[4] + gM[1][1] * V[5] + gM[1][2] * V[6];
+    T gJ12 = gM[1][0] * V[8] + gM[1][1] * V[9] + gM[1][2] * V[10];
+    T tz = f.t[2], itz = (T)1 / tz, itz2 = itz * itz;
+    T fx = cam.fx, fy = cam.fy;
+    T gt[3] = {0, 0, 0};
+    gt[2] -= (gJ00 * fx + gJ11 * fy) * itz2;
+    if (!f.clx) { gt[0] -= gJ02 * fx * itz2; gt[2] += 2 * gJ02 * fx * f.t[0] * itz2 * itz; }
+    else { gt[2] += gJ02 * fx * f.uxc * itz2; }
+    if (!f.cly) { gt[1] -= gJ12 * fy * itz2; gt[2] += 2 * gJ12 * fy * f.t[1] * itz2 * itz; }
+    else { gt[2] += gJ12 * fy * f.uyc * itz2; }
+    // mu-hat = (fx tx/tz + cx, fy ty/tz + cy)
+    gt[0] += (T)g2[0] * fx * itz;
+    gt[1] += (T)g2[1] * fy * itz;
+    gt[2] -= ((T)g2[0] * fx * f.t[0] + (T)g2[1] * fy * f.t[1]) * itz2;
+    // t = W mu + t_c
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gm[j] += (float)(V[j] * gt[0] + V[4 + j] * gt[1] + V[8 + j] * gt[2]);
+}
+
+__global__ void __launch_bounds__(kProjBlock) k_project_bwd(ProjBwdLaunch p) {
+    const int n = p.g.n;
+    const int i = blockIdx.x * kProjBlock + threadIdx.x;
+    if (i >= n) return;
+    float m[3], s[3], nrm[3], q[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m[k] = __ldg(p.g.means + 3 * (size_t)i + k);
+        s[k] = __ldg(p.g.scales + 3 * (size_t)i + k);
+        nrm[k] = __ldg(p.g.normals + 3 * (size_t)i + k);
+    }
+    float4 q4 = __ldg(reinterpret_cast<const float4 *>(p.g.quats) + i);
+    q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
+    const int deg = p.g.sh_degree;
+    const int nc = (deg + 1) * (deg + 1);
+    float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gn[3] = {0, 0, 0};
+    float go1 = 0, go2 = 0;
+    float gsh[48];
+#pragma unroll
+    for (int j = 0; j < 48; ++j) gsh[j] = 0.0f;
+    float sh[48];
+    bool sh_loaded = false;
+    const float lp = p.cfg.lowpass;
+
+    for (int v = 0; v < p.n_views; ++v) {
+        const size_t vi = (size_t)v * n + i;
+        const float4 *g4 = reinterpret_cast<const float4 *>(p.grad2d) + 3 * vi;
+        float4 a = g4[0], b = g4[1], c = g4[2];
+        float g2[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) any |= (g2[j] != 0.0f);
+        if (!any) continue;
+        const hgs_camera &cam = p.cams[v];
+        go1 += g2[7];
+        go2 += g2[8];
+        Proj<float> f;
+        f.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
+        if (f.degenerate()) {
+            Proj<double> d;
+            d.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
+            proj_vjp<double>(d, s, cam, g2, gm, gs, gq, gn);
+        } else {
+            proj_vjp<float>(f, s, cam, g2, gm, gs, gq, gn);
+        }
+        // SH colour
+        if (!sh_loaded) {
+#pragma unroll
+            for (int j = 0; j < 48; ++j)
+                if (j < nc * 3) sh[j] = __ldg(p.g.sh + (size_t)i * nc * 3 + j);
+            sh_loaded = true;
+        }
+        float cpos[3];
+        camera_centre(cam, cpos);
+        float dv[3] = {m[0] - cpos[0], m[1] - cpos[1], m[2] - cpos[2]};
+        float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        float dir[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
+        float Y[16], dY[16][3];
+        sh_basis(deg, dir[0], dir[1], dir[2], Y);
+        sh_basis_grad(deg, dir[0], dir[1], dir[2], dY);
+        float graw[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < 16; ++l)
+                if (l < nc) acc += sh[3 * l + ch] * Y[l];
+            graw[ch] = (acc + 0.5f < 0.0f) ? 0.0f : g2[9 + ch];
+        }
+        float gd[3] = {0, 0, 0};
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            if (l >= nc) break;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                gsh[3 * l + ch] += graw[ch] * Y[l];
+                float cg = graw[ch] * sh[3 * l + ch];
+                gd[0] += cg * dY[l][0]; gd[1] += cg * dY[l][1]; gd[2] += cg * dY[l][2];
+            }
+        }
+        float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gm[k] += (gd[k] - dd * dir[k]) * il;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p.out.means[3 * (size_t)i + k] = gm[k];
+        p.out.scales[3 * (size_t)i + k] = gs[k];
+        p.out.normals[3 * (size_t)i + k] = gn[k];
+    }
+    reinterpret_cast<float4 *>(p.out.quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+    p.out.opac1[i] = go1;
+    p.out.opac2[i] = go2;
+#pragma unroll
+    for (int j = 0; j < 48; ++j)
+        if (j < nc * 3) p.out.sh[(size_t)i * nc * 3 + j] = gsh[j];
+}
+
+}  // namespace
+
+cudaError_t launch_project(const ProjLaunch &p, cudaStream_t s) {
+    if (p.g.n == 0) return cudaSuccess;
+    dim3 grid(div_up(p.g.n, kProjBlock));
+    k_project<<<grid, kProjBlock, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const ProjBwdLaunch &p, cudaStream_t s) {
+    if (p.g.n == 0) return cudaSuccess;
+    dim3 grid(div_up(p.g.n, kProjBlock));
+    k_project_bwd<<<grid, kProjBlock, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace hgs

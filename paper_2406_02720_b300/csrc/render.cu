@@ -1,0 +1,487 @@
+// Per-pixel compositing of half-Gaussian splats (A6) and its adjoint (A7).
+//
+// One thread block per tile (one thread per pixel).  The tile's depth-sorted
+// list is walked in batches that the block stages in shared memory.  For each
+// (pixel, splat) pair:
+//   d = p - mu-hat,  hat G = exp(-1/2 d^T conic d)             (Eq. 4-5)
+//   P = 1/2 erfc(-w'.d)                                         (Eq. 7-8)
+//   a = min(0.99, (alpha2 + (alpha1 - alpha2) P) hat G)          (Eq. 10)
+// composited front to back (Sec. 3.3).  A splat with a < 1/255 is skipped, and
+// a splat that would take T below 1e-4 ends the pixel's list (3D-GS rules).
+// A block stops once every pixel in it has finished (__syncthreads_count).
+//
+// erfc comes from Abramowitz & Stegun, Handbook of Mathematical Functions, 7.1.26
+// (|error| <= 1.5e-7 on erf), which needs exp(-z^2); the backward reuses that
+// exponential for dP/dz = exp(-z^2)/sqrt(pi).  Exponentials use the ex2.approx
+// instruction with the conic pre-scaled by log2(e).  Forward and backward
+// evaluate the same inline function with explicit _rn intrinsics, so their
+// per-splat decisions are bit-identical.
+//
+// The backward walks each pixel's list back to front from its last composited
+// splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i),
+// reduces the 12 screen-space gradients over the warp and issues three float4
+// atomics per (warp, splat).
+//
+// Persistent mode: a grid of resident blocks pops global tile ids from an
+// atomic queue whose order is heaviest-first (bucketed by list length).
+#include <algorithm>
+
+#include "hgs_internal.cuh"
+
+namespace hgs {
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kInvSqrtPi = 0.56418958354775628f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kStepDetect = 1e20f;     // |w'| beyond this: step-mode splat (no dP)
+// Abramowitz & Stegun 7.1.26
+constexpr float kAsP = 0.3275911f;
+constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f;
+constexpr float kAs4 = -1.453152027f, kAs5 = 1.061405429f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int BATCH>
+struct Batch {
+    float mx[BATCH], my[BATCH];
+    float ha[BATCH], nb[BATCH], hc[BATCH];   // conic scaled by -log2(e)/2, -log2(e), -log2(e)/2
+    float wx[BATCH], wy[BATCH];
+    float a2[BATCH], da[BATCH];              // alpha2, alpha1 - alpha2
+    float cut[BATCH];                        // skip when the log2 exponent is below this
+    float r[BATCH], g[BATCH], b[BATCH];
+};
+
+template <int BATCH>
+struct BwdExtra {
+    float qa[BATCH], qb[BATCH], qc[BATCH];
+    uint32_t id[BATCH];
+};
+
+template <int BATCH>
+__device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH> &s, int k) {
+    const float4 r0 = __ldg(rec + 3 * (size_t)id);
+    const float4 r1 = __ldg(rec + 3 * (size_t)id + 1);
+    const float4 r2 = __ldg(rec + 3 * (size_t)id + 2);
+    s.mx[k] = r0.x;
+    s.my[k] = r0.y;
+    s.ha[k] = __fmul_rn(-0.5f * kLog2e, r0.z);
+    s.nb[k] = __fmul_rn(-kLog2e, r0.w);
+    s.hc[k] = __fmul_rn(-0.5f * kLog2e, r1.x);
+    s.wx[k] = r1.y;
+    s.wy[k] = r1.z;
+    const float a1 = r1.w, a2 = r2.x;
+    s.a2[k] = a2;
+    s.da[k] = __fsub_rn(a1, a2);
+    const float amax = fmaxf(a1, a2);
+    // alpha <= amax * G < 1/255 whenever log2 G < -log2(255 amax); 1e-3 covers ex2/lg2 error
+    s.cut[k] = amax > 0.0f ? __fsub_rn(-lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : __int_as_float(0x7f800000);
+    s.r[k] = r2.y;
+    s.g[k] = r2.z;
+    s.b[k] = r2.w;
+}
+
+struct Eval {
+    float a, G, P, A, dx, dy, e;
+    bool clamped;
+};
+
+// The per-(pixel, splat) weight of Eq. 10; true if the splat is composited
+// (a >= 1/255).  Identical instruction sequence in forward and backward.
+template <int BATCH>
+__device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const Batch<BATCH> &s, int k, Eval &ev) {
+    const float dx = __fsub_rn(fpx, s.mx[k]);
+    const float dy = __fsub_rn(fpy, s.my[k]);
+    const float p2 = __fmaf_rn(dx, __fmaf_rn(s.ha[k], dx, __fmul_rn(s.nb[k], dy)),
+                               __fmul_rn(__fmul_rn(s.hc[k], dy), dy));
+    if (p2 > 0.0f || p2 < s.cut[k]) return false;
+    const float G = ex2_approx(p2);
+    const float z = __fmaf_rn(s.wx[k], dx, __fmul_rn(s.wy[k], dy));
+    const float u = fabsf(z);
+    const float t = rcp_approx(__fmaf_rn(kAsP, u, 1.0f));
+    float poly = __fmaf_rn(kAs5, t, kAs4);
+    poly = __fmaf_rn(poly, t, kAs3);
+    poly = __fmaf_rn(poly, t, kAs2);
+    poly = __fmaf_rn(poly, t, kAs1);
+    poly = __fmul_rn(poly, t);
+    const float e = ex2_approx(__fmul_rn(-kLog2e, __fmul_rn(u, u)));   // exp(-z^2)
+    const float y = __fmul_rn(poly, e);                                   // erfc(|z|)
+    const float P = z >= 0.0f ? __fsub_rn(1.0f, __fmul_rn(0.5f, y)) : __fmul_rn(0.5f, y);
+    const float A = __fmaf_rn(s.da[k], P, s.a2[k]);
+    const float araw = __fmul_rn(A, G);
+    ev.clamped = araw > kAlphaMax;
+    ev.a = ev.clamped ? kAlphaMax : araw;
+    ev.G = G; ev.P = P; ev.A = A; ev.dx = dx; ev.dy = dy; ev.e = e;
+    return ev.a >= kAlphaMin;
+}
+
+struct TileInfo {
+    int view, tx, ty, W, H;
+    uint32_t beg, end;
+    long long pix_off;
+    float bg[3];
+};
+
+template <int TW, int TH>
+__device__ __forceinline__ TileInfo tile_info(const RenderLaunch &p, int gtile) {
+    TileInfo ti;
+    ti.view = view_of_tile(p.vt, gtile);
+    const int local = gtile - p.vt.tile_off[ti.view];
+    const int tx_n = p.vt.tiles_x[ti.view];
+    ti.tx = local % tx_n;
+    ti.ty = local / tx_n;
+    const hgs_camera &cam = p.cams[ti.view];
+    ti.W = cam.width;
+    ti.H = cam.height;
+    ti.bg[0] = cam.bg[0]; ti.bg[1] = cam.bg[1]; ti.bg[2] = cam.bg[2];
+    ti.beg = p.ranges[2 * (size_t)gtile];
+    ti.end = p.ranges[2 * (size_t)gtile + 1];
+    if (ti.end < ti.beg) ti.end = ti.beg;
+    ti.pix_off = p.vt.pix_off[ti.view];
+    return ti;
+}
+
+// ---- forward -------------------------------------------------------------------------
+template <int TW, int TH, int BATCH>
+__device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s) {
+    constexpr int NT = TW * TH;
+    const int tid = threadIdx.x;
+    const TileInfo ti = tile_info<TW, TH>(p, gtile);
+    const int px = ti.tx * TW + tid % TW, py = ti.ty * TH + tid / TW;
+    const bool inside = px < ti.W && py < ti.H;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
+    const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (uint32_t base = ti.beg; base < ti.end; base += BATCH) {
+        if (__syncthreads_count(done) == NT) break;
+        for (int k = tid; k < BATCH; k += NT) {
+            const uint32_t j = base + k;
+            if (j < ti.end) {
+                uint32_t id = p.ids[j];
+                if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
+                stage<BATCH>(rec, id, s, k);
+            }
+        }
+        __syncthreads();
+        if (!done) {
+            const int cnt = (int)min((uint32_t)BATCH, ti.end - base);
+            for (int k = 0; k < cnt; ++k) {
+                Eval ev;
+                if (!eval_alpha<BATCH>(fpx, fpy, s, k, ev)) continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
+                if (Tn < kTMin) { done = true; break; }
+                const float w = __fmul_rn(ev.a, T);
+                C0 = __fmaf_rn(s.r[k], w, C0);
+                C1 = __fmaf_rn(s.g[k], w, C1);
+                C2 = __fmaf_rn(s.b[k], w, C2);
+                T = Tn;
+                last = base - ti.beg + k + 1;
+            }
+        }
+    }
+    if (inside) {
+        const size_t HW = (size_t)ti.W * ti.H;
+        const size_t pix = (size_t)py * ti.W + px;
+        float *img = p.image + 3 * (size_t)ti.pix_off;
+        img[pix] = C0 + T * ti.bg[0];
+        img[HW + pix] = C1 + T * ti.bg[1];
+        img[2 * HW + pix] = C2 + T * ti.bg[2];
+        p.final_T[ti.pix_off + pix] = T;
+        p.n_contrib[ti.pix_off + pix] = last;
+    }
+}
+
+// ---- backward ------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+template <int TW, int TH, int BATCH>
+__device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s,
+                                                BwdExtra<BATCH> &x, uint32_t &s_maxlast) {
+    constexpr int NT = TW * TH;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const TileInfo ti = tile_info<TW, TH>(p, gtile);
+    const int px = ti.tx * TW + tid % TW, py = ti.ty * TH + tid / TW;
+    const bool inside = px < ti.W && py < ti.H;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
+    const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
+    const size_t HW = (size_t)ti.W * ti.H;
+    const size_t pix = (size_t)py * ti.W + px;
+    float T = 1.0f, Tf = 1.0f, g0 = 0, g1 = 0, g2 = 0;
+    uint32_t last = 0;
+    if (inside) {
+        Tf = p.final_T[ti.pix_off + pix];
+        last = p.n_contrib[ti.pix_off + pix];
+        const float *gi = p.dL_dimage + 3 * (size_t)ti.pix_off;
+        g0 = gi[pix]; g1 = gi[HW + pix]; g2 = gi[2 * HW + pix];
+        T = Tf;
+    }
+    if (tid == 0) s_maxlast = 0;
+    __syncthreads();
+    if (last) atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const uint32_t tile_end = min(ti.end, ti.beg + s_maxlast);
+    const float bgg = ti.bg[0] * g0 + ti.bg[1] * g1 + ti.bg[2] * g2;
+    float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
+    float4 *grad4 = reinterpret_cast<float4 *>(p.grad2d);
+    for (uint32_t bend = tile_end; bend > ti.beg;) {
+        const uint32_t bstart = (bend - ti.beg > (uint32_t)BATCH) ? bend - BATCH : ti.beg;
+        __syncthreads();
+        for (int k = tid; k < BATCH; k += NT) {
+            const uint32_t j = bstart + k;
+            if (j < bend) {
+                uint32_t id = p.ids[j];
+                if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
+                stage<BATCH>(rec, id, s, k);
+                const float4 r0 = __ldg(rec + 3 * (size_t)id);
+                x.qa[k] = r0.z;
+                x.qb[k] = r0.w;
+                x.qc[k] = __ldg(rec + 3 * (size_t)id + 1).x;
+                x.id[k] = id;
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)(bend - bstart);
+        for (int k = cnt - 1; k >= 0; --k) {
+            const uint32_t pos = bstart + k - ti.beg;
+            Eval ev;
+            bool contrib = inside && pos < last && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+            float gr[12];
+#pragma unroll
+            for (int f = 0; f < 12; ++f) gr[f] = 0.0f;
+            if (contrib) {
+                const float one_m_a = __fsub_rn(1.0f, ev.a);
+                const float Ti = __fdividef(T, one_m_a);
+                const float w = ev.a * Ti;
+                gr[9] = w * g0; gr[10] = w * g1; gr[11] = w * g2;
+                float dLda = Ti * ((s.r[k] - S0) * g0 + (s.g[k] - S1) * g1 + (s.b[k] - S2) * g2);
+                dLda -= __fdividef(Tf * bgg, one_m_a);
+                S0 = ev.a * s.r[k] + one_m_a * S0;
+                S1 = ev.a * s.g[k] + one_m_a * S1;
+                S2 = ev.a * s.b[k] + one_m_a * S2;
+                T = Ti;
+                if (!ev.clamped) {
+                    const float dA = dLda * ev.G;
+                    gr[7] = dA * ev.P;
+                    gr[8] = dA - gr[7];
+                    const float dpow = dLda * ev.A * ev.G;
+                    const float dx = ev.dx, dy = ev.dy;
+                    gr[2] = -0.5f * dpow * dx * dx;
+                    gr[3] = -dpow * dx * dy;
+                    gr[4] = -0.5f * dpow * dy * dy;
+                    gr[0] = dpow * (x.qa[k] * dx + x.qb[k] * dy);
+                    gr[1] = dpow * (x.qb[k] * dx + x.qc[k] * dy);
+                    if (fabsf(s.wx[k]) + fabsf(s.wy[k]) < kStepDetect) {
+                        const float dz = dA * s.da[k] * ev.e * kInvSqrtPi;
+                        gr[5] = dz * dx;
+                        gr[6] = dz * dy;
+                        gr[0] -= dz * s.wx[k];
+                        gr[1] -= dz * s.wy[k];
+                    }
+                }
+            }
+            const unsigned any = __ballot_sync(0xffffffffu, contrib);
+            if (any) {
+#pragma unroll
+                for (int f = 0; f < 12; ++f) gr[f] = warp_sum(gr[f]);
+                if (lane == 0) {
+                    float4 *dst = grad4 + 3 * (size_t)x.id[k];
+                    atomicAdd(dst, make_float4(gr[0], gr[1], gr[2], gr[3]));
+                    atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
+                    atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
+                }
+            }
+        }
+        bend = bstart;
+    }
+}
+
+// ---- kernels ------------------------------------------------------------------------
+struct Queue {
+    uint32_t counter_fwd, counter_bwd;
+    uint32_t bucket_count[33];
+    uint32_t bucket_cursor[33];
+};
+
+template <int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(TW *TH) k_render_fwd(RenderLaunch p) {
+    __shared__ Batch<BATCH> s;
+    if (!p.cfg.persistent) {
+        render_tile_fwd<TW, TH, BATCH>(p, blockIdx.x, s);
+        return;
+    }
+    Queue *q = reinterpret_cast<Queue *>(p.ws);
+    const uint32_t *order = reinterpret_cast<const uint32_t *>(q + 1);
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&q->counter_fwd, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= (uint32_t)p.vt.total_tiles) break;
+        render_tile_fwd<TW, TH, BATCH>(p, (int)order[item], s);
+        __syncthreads();
+    }
+}
+
+template <int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(TW *TH) k_render_bwd(RenderLaunch p) {
+    __shared__ Batch<BATCH> s;
+    __shared__ BwdExtra<BATCH> x;
+    __shared__ uint32_t s_maxlast;
+    if (!p.cfg.persistent) {
+        render_tile_bwd<TW, TH, BATCH>(p, blockIdx.x, s, x, s_maxlast);
+        return;
+    }
+    Queue *q = reinterpret_cast<Queue *>(p.ws);
+    const uint32_t *order = reinterpret_cast<const uint32_t *>(q + 1);
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&q->counter_bwd, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= (uint32_t)p.vt.total_tiles) break;
+        render_tile_bwd<TW, TH, BATCH>(p, (int)order[item], s, x, s_maxlast);
+        __syncthreads();
+    }
+}
+
+// Work order for the persistent kernels: tiles bucketed by floor(log2(list length)),
+// heaviest bucket first (empty tiles last).  Order within a bucket is arbitrary;
+// the images do not depend on it.
+__device__ __forceinline__ int cost_bucket(const uint32_t *ranges, int t) {
+    const uint32_t len = ranges[2 * (size_t)t + 1] - ranges[2 * (size_t)t];
+    return len ? 32 - __clz(len) : 0;    // 1..32, 0 for empty
+}
+
+__global__ void k_queue_count(const uint32_t *ranges, int total_tiles, Queue *q) {
+    __shared__ uint32_t h[33];
+    for (int j = threadIdx.x; j < 33; j += blockDim.x) h[j] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[cost_bucket(ranges, t)], 1u);
+    __syncthreads();
+    for (int j = threadIdx.x; j < 33; j += blockDim.x)
+        if (h[j]) atomicAdd(&q->bucket_count[j], h[j]);
+}
+
+__global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, uint32_t *order) {
+    __shared__ uint32_t start[33];
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int b = 32; b >= 0; --b) { start[b] = acc; acc += q->bucket_count[b]; }
+    }
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
+        const int b = cost_bucket(ranges, t);
+        order[start[b] + atomicAdd(&q->bucket_cursor[b], 1u)] = (uint32_t)t;
+    }
+}
+
+template <int TW, int TH, int BATCH>
+cudaError_t launch_fwd_t(const RenderLaunch &p, cudaStream_t s) {
+    if (!p.cfg.persistent) {
+        k_render_fwd<TW, TH, BATCH><<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    static int blocks = 0;
+    if (!blocks) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fwd<TW, TH, BATCH>, TW * TH, 0);
+        blocks = num_sms() * std::max(occ, 1);
+    }
+    k_render_fwd<TW, TH, BATCH><<<std::min(blocks, p.vt.total_tiles), TW * TH, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int TW, int TH, int BATCH>
+cudaError_t launch_bwd_t(const RenderLaunch &p, cudaStream_t s) {
+    if (!p.cfg.persistent) {
+        k_render_bwd<TW, TH, BATCH><<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    static int blocks = 0;
+    if (!blocks) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_bwd<TW, TH, BATCH>, TW * TH, 0);
+        blocks = num_sms() * std::max(occ, 1);
+    }
+    k_render_bwd<TW, TH, BATCH><<<std::min(blocks, p.vt.total_tiles), TW * TH, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_queue(const RenderLaunch &p, cudaStream_t s) {
+    Queue *q = reinterpret_cast<Queue *>(p.ws);
+    uint32_t *order = reinterpret_cast<uint32_t *>(q + 1);
+    cudaError_t e = cudaMemsetAsync(q, 0, sizeof(Queue), s);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(div_up(p.vt.total_tiles, 256), 4 * num_sms());
+    k_queue_count<<<grid, 256, 0, s>>>(p.ranges, p.vt.total_tiles, q);
+    k_queue_fill<<<grid, 256, 0, s>>>(p.ranges, p.vt.total_tiles, q, order);
+    return cudaGetLastError();
+}
+
+// dispatch over the supported (tile shape, batch) combinations
+template <bool FWD, int TW, int TH>
+cudaError_t dispatch_batch(const RenderLaunch &p, cudaStream_t s) {
+    const int batch = p.cfg.batch ? p.cfg.batch : TW * TH;
+    switch (batch) {
+        case 32: return FWD ? launch_fwd_t<TW, TH, 32>(p, s) : launch_bwd_t<TW, TH, 32>(p, s);
+        case 64: return FWD ? launch_fwd_t<TW, TH, 64>(p, s) : launch_bwd_t<TW, TH, 64>(p, s);
+        case 128: return FWD ? launch_fwd_t<TW, TH, 128>(p, s) : launch_bwd_t<TW, TH, 128>(p, s);
+        case 256: return FWD ? launch_fwd_t<TW, TH, 256>(p, s) : launch_bwd_t<TW, TH, 256>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool FWD>
+cudaError_t dispatch(const RenderLaunch &p, cudaStream_t s) {
+    if (p.vt.total_tiles == 0) return cudaSuccess;
+    if (p.cfg.persistent) {
+        cudaError_t e = prepare_queue(p, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int tw = p.cfg.tile_w, th = p.cfg.tile_h;
+    if (tw == 16 && th == 16) return dispatch_batch<FWD, 16, 16>(p, s);
+    if (tw == 8 && th == 8) return dispatch_batch<FWD, 8, 8>(p, s);
+    if (tw == 32 && th == 8) return dispatch_batch<FWD, 32, 8>(p, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t render_workspace_bytes(const ViewTable &vt, const hgs_config &cfg) {
+    (void)cfg;
+    return sizeof(Queue) + 4 * (size_t)std::max(vt.total_tiles, 1) + 256;
+}
+
+cudaError_t launch_render_fwd(const RenderLaunch &p, cudaStream_t s) { return dispatch<true>(p, s); }
+cudaError_t launch_render_bwd(const RenderLaunch &p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 12 * (size_t)p.n * p.vt.n_views, s);
+    if (e != cudaSuccess) return e;
+    return dispatch<false>(p, s);
+}
+
+}  // namespace hgs

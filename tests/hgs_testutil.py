@@ -1,0 +1,74 @@
+"""Shared helpers for the GPU parity tests: run the CUDA path through the C ABI
+and the FP64 oracle on the same seeded inputs, and compare."""
+import numpy as np
+
+import oracle
+
+# A pixel whose oracle decisions (1/255 floor, 1e-4 stop, step-mode sign) sit
+# within this relative distance of their threshold can flip between FP32 and FP64.
+EXEMPT_MARGIN = 1e-4
+IMAGE_ATOL = 1e-4
+
+
+def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persistent=False,
+               pair_capacity=None, dL=None):
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
+    cfg = H.make_config(tile=tile, batch=batch, lowpass=lowpass, plain=plain, persistent=persistent)
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(cams, sc.n, cfg, pair_capacity=pair_capacity)
+    r.forward(g)
+    out = dict(rast=r, g=g)
+    out["images"] = [x.cpu().numpy() for x in r.images()]
+    out["T"] = [x.cpu().numpy() for x in r.per_pixel(r.final_T)]
+    out["n_contrib"] = [x.cpu().numpy() for x in r.per_pixel(r.n_contrib)]
+    k, i = r.sorted_pairs()
+    out["keys"] = k.cpu().numpy().view(np.uint64)
+    out["ids"] = i.cpu().numpy().view(np.uint32)
+    out["ranges"] = r.ranges.cpu().numpy().view(np.uint32)
+    out["rec"] = r.rec.cpu().numpy().reshape(len(cams), sc.n, 12)
+    out["depth"] = r.depth.cpu().numpy().reshape(len(cams), sc.n)
+    out["rect"] = r.rect.cpu().numpy().reshape(len(cams), sc.n, 4)
+    out["tiles"] = r.tiles.cpu().numpy().reshape(len(cams), sc.n)
+    if dL is not None:
+        flat = np.concatenate([np.asarray(d, np.float32).reshape(-1) for d in dL])
+        dl = torch.from_numpy(flat).cuda()
+        gr = r.backward(g, dl)
+        out["grads"] = {k2: getattr(gr, k2).cpu().numpy().astype(np.float64) for k2 in
+                        ("means", "scales", "quats", "normals", "opac1", "opac2", "sh")}
+        out["grad2d"] = r.grad2d.cpu().numpy().reshape(len(cams), sc.n, 12)
+    torch.cuda.synchronize()
+    return out
+
+
+def compare_image(gpu_img, gpu_T, gpu_nc, ref, atol=IMAGE_ATOL, max_exempt_frac=1e-3):
+    """Max-abs image/T error on pixels away from threshold decisions; n_contrib equal there."""
+    ok = ref["margin"] > EXEMPT_MARGIN
+    n_ex = int((~ok).sum())
+    assert n_ex <= max(4, max_exempt_frac * ok.size), f"{n_ex} exempt pixels of {ok.size}"
+    err = np.abs(gpu_img.astype(np.float64) - ref["image"])[:, ok]
+    terr = np.abs(gpu_T.astype(np.float64) - ref["T"])[ok]
+    assert err.size == 0 or err.max() <= atol, f"image max abs err {err.max():.3g}"
+    assert terr.size == 0 or terr.max() <= atol, f"T max abs err {terr.max():.3g}"
+    assert np.array_equal(gpu_nc[ok], ref["n_contrib"][ok])
+    return dict(max_err=float(err.max()) if err.size else 0.0, exempt=n_ex)
+
+
+def grad_close(g, ref, rel=1e-3, floor_frac=1e-3):
+    """|g - ref| <= rel * max(|ref|, floor_frac * max|ref|) elementwise."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = np.maximum(np.abs(ref), floor_frac * max(np.abs(ref).max(), 1e-30))
+    bad = np.abs(g - ref) > rel * scale
+    return bad, scale
+
+
+def masked_upstream(dL_list, refs):
+    """dL/dimage with exempt pixels zeroed (both sides get the same array)."""
+    out = []
+    for d, r in zip(dL_list, refs):
+        d = np.array(d, np.float32, copy=True)
+        d[:, r["margin"] <= EXEMPT_MARGIN] = 0.0
+        out.append(d)
+    return out

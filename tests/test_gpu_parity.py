@@ -1,0 +1,202 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: sort order, tile ranges, depth keys and tile rects bit-exact; images and
+final transmittance within 1e-4 max-abs on pixels whose decisions are not
+within 1e-4 (relative) of a threshold; n_contrib equal there; gradients within
+1e-3 relative (floor 1e-3 of the tensor's largest entry) of the FP64 adjoint,
+with the upstream gradient zeroed on the exempt pixels.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from hgs_testutil import compare_image, gpu_render, grad_close, masked_upstream
+from paper_2406_02720_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged_scene(seed=21, n=1500):
+    rng = np.random.default_rng(seed)
+    sc = scenes.scene_uniform(rng, n, [-1.6, -1.2, 2], [1.6, 1.2, 7], -3.0, 0.6, 1.2, 1)
+    return sc, [scenes.identity_camera(100, 75, 70.0, 51.0, 36.5, bg=(0.1, 0.2, 0.3))]
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return scenes.config1()
+
+
+def test_projection_fields(cuda_ok, cfg1):
+    sc, cams = cfg1
+    out = gpu_render(sc, cams)
+    pr = oracle.project(sc, cams[0])
+    assert np.array_equal(out["tiles"][0], pr["tiles"].astype(np.int32))
+    vis = pr["tiles"] > 0
+    assert np.array_equal(out["depth"][0].view(np.uint32), pr["depth"].view(np.uint32))
+    assert np.array_equal(out["rect"][0][vis], pr["rect"][vis])
+    rec = out["rec"][0]
+    assert np.array_equal(rec[vis, 0:2].view(np.uint32), pr["canon_mu"][vis].view(np.uint32))
+    Q = rec[vis, 2:5].astype(np.float64)
+    Qr = pr["conic"][vis]
+    assert np.all(np.abs(Q - Qr).max(1) <= 2e-4 * np.abs(Qr).max(1))
+    normal = pr["mode"][vis] == oracle.NORMAL
+    wp = rec[vis, 5:7].astype(np.float64)[normal]
+    wr = pr["wp"][vis][normal]
+    assert np.all(np.abs(wp - wr).max(1) <= 1e-3 * np.maximum(np.abs(wr).max(1), 1e-3))
+    np.testing.assert_allclose(rec[vis, 9:12], pr["rgb"][vis], atol=2e-6)
+    np.testing.assert_array_equal(rec[vis, 7], sc.opac1[vis])
+    np.testing.assert_array_equal(rec[vis, 8], sc.opac2[vis])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_binning_bit_exact(cuda_ok, tile):
+    sc, cams = _ragged_scene()
+    out = gpu_render(sc, cams, tile=tile)
+    ref = oracle.bin_pairs(oracle.project(sc, cams[0], tile=tile), cams[0], tile)
+    assert out["keys"].size == ref["n_pairs"] > 1000
+    assert np.array_equal(out["keys"], ref["keys"])
+    assert np.array_equal(out["ids"], ref["ids"])
+    assert np.array_equal(out["ranges"], ref["ranges"])
+
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 0), ((8, 8), 32), ((32, 8), 128), ((16, 16), 64)])
+def test_forward_image_ragged(cuda_ok, tile, batch):
+    sc, cams = _ragged_scene()
+    out = gpu_render(sc, cams, tile=tile, batch=batch)
+    ref = oracle.render(sc, cams[0], tile=tile)
+    info = compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    assert ref["n_contrib"].max() > 5
+
+
+def test_forward_config1(cuda_ok, cfg1):
+    sc, cams = cfg1
+    out = gpu_render(sc, cams)
+    ref = oracle.render(sc, cams[0])
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    assert (ref["T"] < 0.01).mean() > 0.01      # early termination happens in this scene
+
+
+def test_equal_opacity_is_bitwise_plain_3dgs(cuda_ok):
+    sc, cams = _ragged_scene(seed=5)
+    sc.opac2[:] = sc.opac1
+    a = gpu_render(sc, cams)
+    b = gpu_render(sc, cams, plain=True)
+    assert np.array_equal(a["images"][0], b["images"][0])
+    assert np.array_equal(a["n_contrib"][0], b["n_contrib"][0])
+    rng = np.random.default_rng(3)
+    dL = [rng.standard_normal((3, 75, 100)).astype(np.float32)]
+    ga = gpu_render(sc, cams, dL=dL)["grads"]
+    assert np.all(ga["normals"] == 0.0)
+
+
+def test_complement_symmetry(cuda_ok):
+    sc, cams = _ragged_scene(seed=6)
+    b = scenes.Scene(sc.means, sc.scales, sc.quats, -sc.normals, sc.opac2.copy(), sc.opac1.copy(), sc.sh,
+                     sc.sh_degree)
+    ra, rb = gpu_render(sc, cams), gpu_render(b, cams)
+    ref = oracle.render(sc, cams[0])
+    ok = ref["margin"] > 1e-4
+    assert np.abs(ra["images"][0] - rb["images"][0])[:, ok].max() <= 1e-6
+
+
+def test_gradients_against_fp64_adjoint(cuda_ok):
+    rng = np.random.default_rng(31)
+    sc = scenes.scene_uniform(rng, 800, [-1.3, -0.8, 2.5], [1.3, 0.8, 6], -3.3, 0.5, 1.5, 3)
+    cams = [scenes.identity_camera(160, 96, 90.0, 80.0, 48.0, bg=(0.3, 0.2, 0.1))]
+    ref = oracle.render(sc, cams[0])
+    dL = masked_upstream(scenes.upstream_grad(102, cams), [ref])
+    out = gpu_render(sc, cams, dL=dL)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    gref = oracle.render_bwd(sc, cams[0], dL[0], proj=ref["proj"], bins=ref["bins"])
+    # screen-space gradients first (compositing adjoint), then parameters
+    g2 = out["grad2d"][0]
+    vis = ref["proj"]["mode"] == oracle.NORMAL
+    bad, _ = grad_close(g2[vis], gref["grad2d"][vis])
+    assert bad.mean() < 2e-3, f"grad2d: {bad.sum()} of {bad.size}"
+    report = {}
+    for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
+        bad, _ = grad_close(out["grads"][k], gref[k])
+        report[k] = (int(bad.sum()), bad.size)
+        assert bad.mean() < 2e-3, (k, report[k])
+
+
+def test_multiview_persistent_matches_per_tile_launch(cuda_ok):
+    rng = np.random.default_rng(41)
+    sc = scenes.scene_uniform(rng, 3000, [-2, -2, -2], [2, 2, 2], -3.5, 0.6, 1.5, 2)
+    sizes = [(120, 72), (64, 48), (200, 110)]
+    cams = []
+    for k, (w, h) in enumerate(sizes):
+        c = scenes.fibonacci_cameras(3, radius=6.0, resolutions=[(w, h)])[k]
+        cams.append(c)
+    a = gpu_render(sc, cams, persistent=False)
+    b = gpu_render(sc, cams, persistent=True)
+    for v in range(3):
+        assert np.array_equal(a["images"][v], b["images"][v])
+        assert np.array_equal(a["n_contrib"][v], b["n_contrib"][v])
+    # each view against its own oracle run
+    for v, cam in enumerate(cams):
+        ref = oracle.render(sc, cam)
+        compare_image(b["images"][v], b["T"][v], b["n_contrib"][v], ref)
+    # global sort: the keys of view v are the oracle keys shifted by the view's tile offset
+    off = 0
+    for v, cam in enumerate(cams):
+        tx, ty = oracle.grid(cam, (16, 16))
+        ref = oracle.bin_pairs(oracle.project(sc, cam), cam)
+        sel = (b["keys"] >> np.uint64(32)) - np.uint64(off)
+        m = (b["keys"] >> np.uint64(32) >= off) & (b["keys"] >> np.uint64(32) < off + tx * ty)
+        want = ref["keys"] + (np.uint64(off) << np.uint64(32))
+        assert np.array_equal(b["keys"][m], want)
+        assert np.array_equal(b["ids"][m], ref["ids"] + np.uint32(v * sc.n))
+        off += tx * ty
+
+
+def test_multiview_gradients_sum_over_views(cuda_ok):
+    rng = np.random.default_rng(43)
+    sc = scenes.scene_uniform(rng, 600, [-1.5, -1.5, -1.5], [1.5, 1.5, 1.5], -3.2, 0.5, 1.5, 1)
+    cams = scenes.fibonacci_cameras(2, radius=5.0, resolutions=[(96, 64)])
+    refs = [oracle.render(sc, c) for c in cams]
+    dL = masked_upstream(scenes.upstream_grad(7, cams), refs)
+    out = gpu_render(sc, cams, dL=dL, persistent=True)
+    tot = None
+    for c, d, r in zip(cams, dL, refs):
+        g = oracle.render_bwd(sc, c, d, proj=r["proj"], bins=r["bins"])
+        tot = g if tot is None else {k: tot[k] + g[k] for k in tot}
+    for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
+        bad, _ = grad_close(out["grads"][k], tot[k])
+        assert bad.mean() < 2e-3, k
+
+
+def test_capacity_overflow_sets_status_and_count(cuda_ok):
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
+    sc, cams = scenes.config1()
+    r = Rasterizer(cams, sc.n, H.make_config(), pair_capacity=100)
+    g = Gaussians.from_scene(sc)
+    r.clear_status()
+    r.project(g)
+    r.bin()
+    st = r.read_status()
+    ref = oracle.bin_pairs(oracle.project(sc, cams[0]), cams[0])
+    assert st & H.HGS_DEV_CAPACITY
+    assert int(r.num_pairs.item()) == ref["n_pairs"]
+    # the high-level forward grows the buffer and succeeds
+    r.forward(g)
+    assert r.capacity >= ref["n_pairs"]
+    k, i = r.sorted_pairs()
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ref["keys"])
+    torch.cuda.synchronize()
+
+
+def test_empty_and_all_culled(cuda_ok):
+    sc, cams = scenes.config1()
+    behind = sc.subset(np.arange(50))
+    behind.means[:, 2] = -3.0                      # behind the camera: all culled
+    out = gpu_render(behind, cams)
+    assert out["keys"].size == 0
+    assert np.all(out["images"][0] == 0.0) and np.all(out["T"][0] == 1.0)
+    one = sc.subset(np.arange(1))
+    out = gpu_render(one, cams)
+    ref = oracle.render(one, cams[0])
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
