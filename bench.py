@@ -1,0 +1,443 @@
+"""Benchmark of the half-Gaussian rasterizer's forward+backward step on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload (default): 3M half-Gaussians, SH degree 3, 1920x1080, one view, the
+scene-scale synthetic scene (50 blobs + 10% uniform, bimodal opacities).  A step
+is project -> bin (scan, keys, onesweep sort, ranges) -> composite -> adjoint
+composite -> projection adjoint, captured once in a CUDA graph and replayed.
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("fwd+bwd ms & Mpixel/s at 3M half-Gaussians 1080p; batched views/s vs per-view; % roofline")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+# ---- distributed plumbing (replicas: no data-path collective) ----------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def max_over_ranks(x: float, dist_mod, device=None) -> float:
+    if dist_mod is None:
+        return float(x)
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(pixels_per_rank: float, n_ranks: int, ms_max: float) -> float:
+    """Whole-job Mpixel/s: pixels of all ranks over the slowest rank's time."""
+    return pixels_per_rank * n_ranks / (ms_max * 1e3)
+
+
+# ---- clocks ------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+        if shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- GPU arm --------------------------------------------------------------------------------
+_SCENE = {}
+
+
+def _scene(args):
+    if args.n not in _SCENE:
+        from paper_2406_02720_b300 import scenes
+        sc, cams = scenes.config3(n=args.n)
+        dL = scenes.upstream_grad(103, cams)[0]
+        _SCENE[args.n] = (sc, cams, dL)
+    return _SCENE[args.n]
+
+
+def run_gpu(args):
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300.rasterizer import Gaussians, GraphStep, Rasterizer
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_mod = init_dist(ws, "nccl")
+    dev = torch.device("cuda", local)
+    sc, cams, dL_np = _scene(args)
+    W, H_ = cams[0].width, cams[0].height
+    pixels = W * H_ * len(cams)
+    cfg = H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch)
+    g = Gaussians.from_scene(sc, dev)
+    rast = Rasterizer(cams, sc.n, cfg, device=dev)
+    rast.forward(g)                                     # sizes the pair buffers
+    n_pairs = int(rast.num_pairs.item())
+    rast._alloc_pairs(int(n_pairs * 1.05) + 4096)
+    dL = torch.from_numpy(dL_np.reshape(-1)).to(dev)
+    grads = Gaussians.empty_like(g)
+
+    # phase events recorded inside the graph (external nodes)
+    names = ["project", "bin", "render_fwd", "render_bwd", "project_bwd"]
+    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(names) + 1)]
+
+    class Step(GraphStep):
+        def _body(self, backward):
+            r = self.rast
+            r.status.zero_()
+            evs[0].record()
+            r.project(self.g)
+            evs[1].record()
+            r.bin()
+            evs[2].record()
+            r.render_fwd()
+            evs[3].record()
+            r.rasterize_bwd(self.dL)
+            evs[4].record()
+            r.project_bwd(self.g, self.grads)
+            evs[5].record()
+
+    step = Step(rast, g, dL, grads)
+    torch.cuda.synchronize()
+    st = rast.read_status()
+    if st:
+        raise RuntimeError(f"device status {st} after capture")
+    for _ in range(args.warmup):
+        step.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K back-to-back replays --------------------------------------------
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if dist_mod:
+        dist_mod.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    t0.record()
+    for _ in range(args.steps):
+        step.replay()
+    t1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist_mod:
+        dist_mod.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    ms_max = max_over_ranks(ms, dist_mod, dev)
+    st = rast.read_status()
+    if st:
+        raise RuntimeError(f"device status {st} in timed region")
+
+    # ---- per-phase times from the in-graph events (K more replays, synced each) ---------
+    ph = {k: [] for k in names}
+    for _ in range(args.steps):
+        step.replay()
+        evs[-1].synchronize()
+        for k, nm in enumerate(names):
+            ph[nm].append(evs[k].elapsed_time(evs[k + 1]))
+    phases = {k: statistics.mean(v) for k, v in ph.items()}
+
+    # ---- forward-only step -------------------------------------------------------------------
+    fwd_step = GraphStep(rast, g, dL, grads, backward=False)
+    for _ in range(3):
+        fwd_step.replay()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        fwd_step.replay()
+    f1.record()
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / args.steps
+
+    # ---- work counters for the roofline (one extra forward, not timed) ------------------
+    stats = rast.stats(dL)
+    roof = roofline(phases, stats, n_pairs, sc.n, clocks)
+
+    # ---- end to end through host buffers --------------------------------------------------
+    e2e = run_e2e(args, rast, g, dL, grads, step, pixels, dev)
+
+    launches = 9 + n_sort_passes(rast.total_tiles)     # project, scan, dup, hist, passes, ranges, fwd, bwd, proj_bwd
+    result = {
+        "metric": METRIC, "value": aggregate_value(pixels, ws, ms_max), "unit": "Mpixel/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded scene shaped like the paper's: 3M kernels in blobs, bimodal half opacities)",
+        "config": {"workload": f"config3: {sc.n} half-Gaussians, SH degree 3, {W}x{H_}, 1 view, fwd+bwd, CUDA graph",
+                   "n_splats": sc.n, "width": W, "height": H_, "views": len(cams),
+                   "tile": f"{args.tile_w}x{args.tile_h}", "batch": args.batch or args.tile_w * args.tile_h,
+                   "pairs": n_pairs, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
+        "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
+        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, n_sort_passes(rast.total_tiles)),
+        "clocks": clocks,
+        "e2e": e2e, "gpu_launches": launches * args.steps,
+    }
+    if rank == 0 and args.cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args)
+    if dist_mod:
+        dist_mod.barrier()
+    return result if rank == 0 else None
+
+
+def n_sort_passes(total_tiles):
+    bits = 1
+    while (1 << bits) < total_tiles:
+        bits += 1
+    return (32 + bits + 7) // 8
+
+
+# Algorithmic operations per counted event of the compositing kernels, counted
+# from the source of eval_alpha / render_tile_fwd / render_tile_bwd (see DESIGN):
+#   visit  : offset, quadratic form, two cut-off compares              9 FP32
+#   full   : Eq. 8 via A&S 7.1.26, Eq. 10 mix, clamp, floor compare     20 FP32 + 3 MUFU
+#   comp   : transmittance update, stop test, colour accumulation       7 FP32
+#   contrib: backward adjoint of one composited pair                   58 FP32 + 2 MUFU
+#   red    : warp reduction of 12 gradients (5 shuffle+add levels,
+#            all 32 lanes)                                            1920 FP32
+OPS = {"fwd": {"fp32": {"fwd_visit": 9, "fwd_full": 20, "fwd_comp": 7}, "mufu": {"fwd_full": 3}},
+       "bwd": {"fp32": {"bwd_visit": 9, "bwd_full": 20, "bwd_contrib": 58, "bwd_warp_red": 1920},
+               "mufu": {"bwd_full": 3, "bwd_contrib": 2}}}
+
+
+def alu_work(stats, key):
+    fp32 = sum(stats[k] * c for k, c in OPS[key]["fp32"].items())
+    mufu = sum(stats[k] * c for k, c in OPS[key]["mufu"].items())
+    return fp32, mufu
+
+
+def roofline(phases, stats, n_pairs, n, clocks):
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    src = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6400.0
+    dom = max(phases, key=phases.get)
+    out = {"dominant": dom, "phase_ms": phases[dom]}
+    if dom in ("render_fwd", "render_bwd") and stats:
+        sms = 148
+        mhz = peaks.get("sm_max_mhz", 2032.0)
+        fp32_peak = sms * 128 * mhz * 1e6 / 1e12          # T FP32 lane-ops / s
+        mufu_peak = sms * 16 * mhz * 1e6 / 1e12           # T MUFU lane-ops / s
+        key = "fwd" if dom == "render_fwd" else "bwd"
+        fp32, mufu = alu_work(stats, key)
+        t = phases[dom] * 1e-3
+        f_fp32 = fp32 / t / 1e12 / fp32_peak
+        f_mufu = mufu / t / 1e12 / mufu_peak
+        if f_fp32 >= f_mufu:
+            out.update({"bound": "alu", "achieved": fp32 / t / 1e12, "peak": fp32_peak, "unit": "T FP32-op/s",
+                        "frac": f_fp32})
+        else:
+            out.update({"bound": "alu", "achieved": mufu / t / 1e12, "peak": mufu_peak, "unit": "T MUFU-op/s",
+                        "frac": f_mufu})
+        out.update({"traffic": None, "frac_fp32": f_fp32, "frac_mufu": f_mufu,
+                    "note": f"peak from 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz; algorithmic ops "
+                            "= counted events x ops per event"})
+    else:
+        bytes_per = {"project": n * (252 + 48 + 4 + 16 + 4), "project_bwd": n * (252 + 48 + 252),
+                     "bin": n_pairs * (12 + 8 + 24 * 6 + 8) + n * 8}
+        b = bytes_per.get(dom, 0)
+        ach = b / (phases[dom] * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "note": src})
+    return out
+
+
+def phase_rooflines(phases, stats, n_pairs, n, n_passes):
+    """HBM fraction of the memory-bound phases and ALU fractions of the compositing
+    phases (each against its own bound; algorithmic bytes/ops per launch)."""
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    bytes_per = {"project": n * (252 + 48 + 4 + 16 + 4),
+                 "bin": n * (4 + 4 + 4 + 16 + 4) + n_pairs * (12 + 8 + 24 * n_passes + 8),
+                 "project_bwd": n * (252 + 48 + 252)}
+    out = {}
+    for k, b in bytes_per.items():
+        out[k] = {"bound": "hbm", "GBs": b / (phases[k] * 1e-3) / 1e9, "frac": b / (phases[k] * 1e-3) / 1e9 / hbm}
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    for key, ph in (("fwd", "render_fwd"), ("bwd", "render_bwd")):
+        fp32, mufu = alu_work(stats, key)
+        t = phases[ph] * 1e-3
+        out[ph] = {"bound": "alu", "frac_fp32": fp32 / t / (148 * 128 * mhz * 1e6),
+                   "frac_mufu": mufu / t / (148 * 16 * mhz * 1e6)}
+    return out
+
+
+def run_e2e(args, rast, g, dL, grads, step, pixels, dev):
+    """Same step with inputs copied from pinned host memory and the image and
+    gradients copied back, every step, inside the timed region."""
+    import torch
+    host_in = [t.detach().cpu().pin_memory() for t in g.tensors()] + [dL.detach().cpu().pin_memory()]
+    dev_in = g.tensors() + [dL]
+    outs = [rast.image] + grads.tensors()
+    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def one():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        step.replay()
+        for h, d in zip(host_out, outs):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(3, args.steps // 2)
+    e0.record()
+    for _ in range(k):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    return {"value": pixels / (ms * 1e3), "unit": "Mpixel/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+# ---- CPU oracle (reported baseline / reference arm) -----------------------------------------
+def cpu_baseline(args, n_tiles_sample=48, seed=5):
+    """FP64 oracle on a bounded sample: full projection and projection adjoint of all
+    splats, compositing and its adjoint on a random sample of tiles; the full-frame
+    time is extrapolated by the tile fraction."""
+    import oracle
+    sc, cams, dL = _scene(args)
+    cam = cams[0]
+    tile = (args.tile_w, args.tile_h)
+    tx, ty = oracle.grid(cam, tile)
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(tx * ty, np.uint8)
+    mask[rng.choice(tx * ty, n_tiles_sample, replace=False)] = 1
+    t0 = time.perf_counter()
+    pr = oracle.project(sc, cam, tile)
+    t1 = time.perf_counter()
+    bins = oracle.bin_pairs(pr, cam, tile, tile_mask=mask)
+    t2 = time.perf_counter()
+    out = oracle.render(sc, cam, tile=tile, tile_mask=mask, proj=pr, bins=bins)
+    t3 = time.perf_counter()
+    g = oracle.render_bwd(sc, cam, dL, tile=tile, tile_mask=mask, proj=pr, bins=bins)
+    t4 = time.perf_counter()
+    frac = n_tiles_sample / float(tx * ty)
+    t_proj, t_bin, t_fwd, t_bwd_all = t1 - t0, t2 - t1, t3 - t2, t4 - t3
+    # render_bwd includes the projection adjoint of every splat; time it apart
+    t5 = time.perf_counter()
+    oracle.project_bwd(sc, cam, pr["mode"], g["grad2d"], tile)
+    t_pbwd = time.perf_counter() - t5
+    t_rbwd = max(t_bwd_all - t_pbwd, 0.0)
+    est = t_proj + t_bin + (t_fwd + t_rbwd) / frac + t_pbwd
+    pixels = cam.width * cam.height
+    return {"value": pixels / (est * 1e6), "unit": "Mpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_tiles_sample} of {tx * ty} tiles (seeded) composited fwd+bwd in FP64; projection and "
+                      f"its adjoint over all {sc.n} splats; full-frame time extrapolated by the tile fraction",
+            "est_frame_s": est, "measured_s": t4 - t0 + t_pbwd}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    vals = []
+    last = None
+    for _ in range(args.warmup):
+        cpu_baseline(args, n_tiles_sample=8)
+    for _ in range(args.steps):
+        last = cpu_baseline(args, n_tiles_sample=8)
+        vals.append(last["value"])
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": (1920 * 1080) / (v * 1e3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"config3: {args.n} half-Gaussians, SH degree 3, 1920x1080, "
+                                                        "1 view, fwd+bwd (FP64 CPU oracle, sampled tiles)"},
+            "cpu_baseline": {"value": v, "unit": "Mpixel/s", "kind": "oracle", "cores": last["cores"],
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=3_000_000)
+    ap.add_argument("--tile-w", type=int, default=16)
+    ap.add_argument("--tile-h", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

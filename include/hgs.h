@@ -225,6 +225,21 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
                           const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
                           const hgs_gaussian_grads *out, int *dev_status, void *stream);
 
+/* ---- measurement ------------------------------------------------------------------- */
+
+/* Work counters for the roofline: runs hgs_render_fwd and hgs_rasterize_bwd (same
+ * outputs, same arithmetic) in variants that also count, into counters[8]
+ * (uint64, zeroed by the call):
+ *   [0] forward (pixel, splat) iterations  [1] forward full evaluations (past the
+ *   3-sigma/opacity cut-off)  [2] splats composited  [3] backward iterations
+ *   [4] backward full evaluations  [5] backward contributing pairs
+ *   [6] warp reductions (each issues 3 float4 atomics)  [7] reserved (0). */
+hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
+                            const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
+                            const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
+                            uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                            unsigned long long *counters, int *dev_status, void *stream);
+
 /* ---- misc ------------------------------------------------------------------- */
 const char *hgs_status_string(hgs_status s);
 int hgs_version(void);

@@ -58,7 +58,7 @@ def lib():
         L.or_bin.restype = c_long
         L.or_render_fwd.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, POINTER(c_uint32),
                                     POINTER(c_uint32), POINTER(OrCamera), POINTER(OrOpts),
-                                    POINTER(c_ubyte), dp, dp, ip, dp]
+                                    POINTER(c_ubyte), dp, dp, ip, dp, dp, dp, ip]
         L.or_render_bwd.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, POINTER(c_uint32),
                                     POINTER(c_uint32), POINTER(OrCamera), POINTER(OrOpts),
                                     POINTER(c_ubyte), dp, dp]
@@ -178,8 +178,9 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     """Forward image: front-to-back compositing of the Eq. 10 pair weights over each
     tile's depth-sorted list (3-sigma tile culling, 1/255 floor, 0.99 clamp, 1e-4 stop).
 
-    Returns image [3,H,W], T [H,W], n_contrib [H,W], margin [H,W] (FP64) and the
-    projection/binning intermediates."""
+    Returns image [3,H,W], T [H,W], n_contrib [H,W], margin [H,W] (FP64; also split
+    into margin_a for the 1/255 floor and margin_T for the 1e-4 stop, with n_comp the
+    number of composited splats) and the projection/binning intermediates."""
     if proj is None:
         proj = project(sc, cam, tile, lowpass, fov_clamp)
     if bins is None:
@@ -191,6 +192,9 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     T = np.zeros((H, W))
     nc = np.zeros((H, W), np.int32)
     mg = np.full((H, W), np.inf)
+    mga = np.full((H, W), np.inf)
+    mgT = np.full((H, W), np.inf)
+    ncomp = np.zeros((H, W), np.int32)
     mask_p = None
     if tile_mask is not None:
         tile_mask = np.ascontiguousarray(tile_mask, dtype=np.uint8)
@@ -203,8 +207,10 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
                         _p(proj["conic"], dp), _p(proj["wp"], dp), _p(proj["rgb"], dp),
                         _p(proj["opac1"], dp), _p(proj["opac2"], dp), _p(ids, c_uint32),
                         _p(bins["ranges"], c_uint32), ctypes.byref(c), ctypes.byref(o), mask_p,
-                        _p(image, dp), _p(T, dp), _p(nc, c_int), _p(mg, dp))
-    return dict(image=image, T=T, n_contrib=nc, margin=mg, proj=proj, bins=bins)
+                        _p(image, dp), _p(T, dp), _p(nc, c_int), _p(mg, dp), _p(mga, dp), _p(mgT, dp),
+                        _p(ncomp, c_int))
+    return dict(image=image, T=T, n_contrib=nc, margin=mg, margin_a=mga, margin_T=mgT, n_comp=ncomp,
+                proj=proj, bins=bins)
 
 
 def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,

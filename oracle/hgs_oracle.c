@@ -591,12 +591,16 @@ static void update_margin(double *margin, double val, double thr)
 /* Renders the tiles selected by tile_mask (all if NULL).
  * image [3,H,W], T [H,W], n_contrib [H,W] (1 + list position of the last
  * composited splat, 0 if none), margin [H,W] (smallest relative distance of
- * any threshold decision to its threshold).                                   */
+ * any threshold decision to its threshold).  Optional (may be NULL):
+ * margin_a [H,W] the same over the 1/255 floor and step-sign decisions only,
+ * margin_T [H,W] over the 1e-4 transmittance stop only, n_comp [H,W] the number
+ * of composited splats.                                                       */
 int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic,
                   const double *wp, const double *rgb, const double *op1, const double *op2,
                   const uint32_t *ids, const uint32_t *ranges, const or_camera *cam,
                   const or_opts *o, const unsigned char *tile_mask,
-                  double *image, double *T_out, int *n_contrib, double *margin)
+                  double *image, double *T_out, int *n_contrib, double *margin,
+                  double *margin_a, double *margin_T, int *n_comp)
 {
     (void)n;
     splats2d_t s = {mode, mu2, conic, wp, rgb, op1, op2};
@@ -612,27 +616,31 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
         for (int py = ty * o->tile_h; py < (ty + 1) * o->tile_h && py < H; ++py)
             for (int px = tx * o->tile_w; px < (tx + 1) * o->tile_w && px < W; ++px) {
                 double pcx = px + 0.5, pcy = py + 0.5;
-                double T = 1.0, C[3] = {0, 0, 0}, mg = 1e300;
-                int last = 0;
+                double T = 1.0, C[3] = {0, 0, 0}, mga = 1e300, mgT = 1e300;
+                int last = 0, ncomp = 0;
                 for (uint32_t j = beg; j < end; ++j) {
                     int i = (int)ids[j];
                     if (mode[i] == OR_CULLED) continue;
                     eval_t e;
-                    if (!eval_splat(&s, i, pcx, pcy, o->plain, &e, &mg)) continue;
-                    update_margin(&mg, e.a, OR_ALPHA_MIN);
+                    if (!eval_splat(&s, i, pcx, pcy, o->plain, &e, &mga)) continue;
+                    update_margin(&mga, e.a, OR_ALPHA_MIN);
                     if (e.a < OR_ALPHA_MIN) continue;
                     double Tn = T * (1.0 - e.a);
-                    update_margin(&mg, Tn, OR_T_MIN);
+                    update_margin(&mgT, Tn, OR_T_MIN);
                     if (Tn < OR_T_MIN) break;
                     for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * e.a * T;
                     T = Tn;
                     last = (int)(j - beg) + 1;
+                    ncomp++;
                 }
                 size_t pix = (size_t)py * W + px;
                 for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = C[ch] + T * cam->bg[ch];
                 T_out[pix] = T;
                 n_contrib[pix] = last;
-                margin[pix] = mg;
+                margin[pix] = mga < mgT ? mga : mgT;
+                if (margin_a) margin_a[pix] = mga;
+                if (margin_T) margin_T[pix] = mgT;
+                if (n_comp) n_comp[pix] = ncomp;
             }
     }
     return 0;

@@ -188,6 +188,7 @@ static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids
     p->dL_dimage = nullptr;
     p->grad2d = nullptr;
     p->status = nullptr;
+    p->counters = nullptr;
     return HGS_OK;
 }
 
@@ -221,6 +222,30 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, c
     p.grad2d = grad2d;
     p.status = dev_status;
     return cuda_status(launch_render_bwd(p, static_cast<cudaStream_t>(stream)));
+}
+
+hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
+                            const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
+                            const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
+                            uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                            unsigned long long *counters, int *dev_status, void *stream) {
+    RenderLaunch p;
+    hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
+    if (st != HGS_OK) return st;
+    if (!image || !final_T || !n_contrib || !dL_dimage || !counters || (n > 0 && (!grad2d || !aligned16(grad2d))))
+        return HGS_ERR_INVALID;
+    p.image = image;
+    p.final_T = final_T;
+    p.n_contrib = n_contrib;
+    p.dL_dimage = dL_dimage;
+    p.grad2d = grad2d;
+    p.status = dev_status;
+    p.counters = counters;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_render_fwd(p, s);
+    if (e == cudaSuccess) e = launch_render_bwd(p, s);
+    return cuda_status(e);
 }
 
 hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host, const hgs_camera *cams_dev,

@@ -117,6 +117,7 @@ struct RenderLaunch {
     const float *dL_dimage;
     float *grad2d;
     int *status;
+    unsigned long long *counters;   // non-null: counting launch (see hgs_render_stats)
 };
 size_t render_workspace_bytes(const ViewTable &vt, const hgs_config &cfg);
 cudaError_t launch_render_fwd(const RenderLaunch &p, cudaStream_t s);

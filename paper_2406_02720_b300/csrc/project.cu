@@ -9,6 +9,14 @@
 //              = 1/2 erfc(-w'.d) with u = L^T n^, var_s = |u|^2, k = P u,
 //              w = hat Sigma^-1 k, v = var_s - k.w, w' = w / sqrt(2 v)
 //   Sec. 3.1   view-dependent SH colour
+// Both determinants are formed from sums of non-negative terms, so thin splats
+// lose no precision to cancellation (p0, p1 are the rows of P):
+//   det hat Sigma = |p0 x p1|^2 + l (|p0|^2 + |p1|^2) + l^2
+//   v = det C3 / det hat Sigma, C3 the covariance of (s, pixel):
+//   det C3 = (u.(p0 x p1))^2 + l (|u x p0|^2 + |u x p1|^2) + l^2 |u|^2
+// The conic is stored as its Cholesky factor U (conic = U^T U,
+// U = [[sqrt(c/det), -b/sqrt(c det)], [0, 1/sqrt(c)]]), so that the exponent is
+// evaluated per pixel as a sum of two squares.
 // The binning fields (depth, mu-hat, hat Sigma, 3-sigma radius, tile rect) use a
 // fixed FP32 operation order with no fused multiply-add (__f*_rn intrinsics), so
 // that the integer decisions they feed are reproducible.  The continuous terms
@@ -24,9 +32,9 @@ namespace {
 constexpr int kProjBlock = 256;
 enum { MODE_CULLED = 0, MODE_NORMAL = 1, MODE_STEP = 2, MODE_HALF = 3 };
 
-// Degeneracy tests that send a splat to the FP64 path.
-constexpr float kDetRelFp64 = 1e-4f;   // det < kDetRelFp64 * a * c
-constexpr float kVRelFp64 = 1e-3f;     // v   < kVRelFp64 * var_s
+// Degeneracy test that sends a splat's half-plane terms to the FP64 path: the
+// splitting plane nearly contains the ray (v < kVRelFp64 * var_s).
+constexpr float kVRelFp64 = 1e-3f;
 // Scale applied to w in step mode (v ~ 0): P becomes a step at w.d = 0.
 constexpr float kStepScale = 1.2089258196146292e24f;   // 2^80
 
@@ -161,6 +169,17 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     o.culled = false;
 }
 
+template <typename T>
+__device__ __forceinline__ void cross3(const T a[3], const T b[3], T o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename T>
+__device__ __forceinline__ T dot3(const T a[3], const T b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
 // Full projection in precision T (FP64 fallback; FP32/FP64 recompute in the
 // backward).  Same mathematics as canon_project plus the half-plane terms, with
 // free operation order.
@@ -212,10 +231,14 @@ struct Proj {
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int kk = 0; kk < 3; ++kk) P[i][kk] = M[i][0] * L[0][kk] + M[i][1] * L[1][kk] + M[i][2] * L[2][kk];
-        a = P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2] + (T)lp;
+        const T n0 = P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2];
+        const T n1 = P[1][0] * P[1][0] + P[1][1] * P[1][1] + P[1][2] * P[1][2];
+        a = n0 + (T)lp;
         b = P[0][0] * P[1][0] + P[0][1] * P[1][1] + P[0][2] * P[1][2];
-        c = P[1][0] * P[1][0] + P[1][1] * P[1][1] + P[1][2] * P[1][2] + (T)lp;
-        det = a * c - b * b;
+        c = n1 + (T)lp;
+        T cr[3];
+        cross3(P[0], P[1], cr);
+        det = dot3(cr, cr) + (T)lp * (n0 + n1) + (T)lp * (T)lp;
         T id = (T)1 / det;
         Q[0] = c * id; Q[1] = -b * id; Q[2] = a * id;
         nn = sqrt((T)nrm[0] * nrm[0] + (T)nrm[1] * nrm[1] + (T)nrm[2] * nrm[2]);
@@ -227,17 +250,21 @@ struct Proj {
         for (int i = 0; i < 3; ++i) nh[i] = (T)nrm[i] * in;
 #pragma unroll
         for (int kk = 0; kk < 3; ++kk) u[kk] = L[0][kk] * nh[0] + L[1][kk] * nh[1] + L[2][kk] * nh[2];
-        var_s = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        k[0] = P[0][0] * u[0] + P[0][1] * u[1] + P[0][2] * u[2];
-        k[1] = P[1][0] * u[0] + P[1][1] * u[1] + P[1][2] * u[2];
+        var_s = dot3(u, u);
+        k[0] = dot3(P[0], u);
+        k[1] = dot3(P[1], u);
         w[0] = Q[0] * k[0] + Q[1] * k[1];
         w[1] = Q[1] * k[0] + Q[2] * k[1];
-        v = var_s - (k[0] * w[0] + k[1] * w[1]);
+        T up0[3], up1[3];
+        cross3(u, P[0], up0);
+        cross3(u, P[1], up1);
+        const T trip = dot3(u, cr);
+        v = (trip * trip + (T)lp * (dot3(up0, up0) + dot3(up1, up1)) + (T)lp * (T)lp * var_s) * id;
         mode = (v <= (T)1e-12 * var_s) ? MODE_STEP : MODE_NORMAL;
     }
 
     __device__ __forceinline__ bool degenerate() const {
-        return det < (T)kDetRelFp64 * a * c || (mode == MODE_NORMAL && v < (T)kVRelFp64 * var_s);
+        return mode == MODE_NORMAL && v < (T)kVRelFp64 * var_s;
     }
 };
 
@@ -363,9 +390,12 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
         p.out.tiles[vi] = cb.culled ? 0u : cb.tiles;
         if (cb.culled || cb.tiles == 0) continue;
 
-        // conic and half-plane terms, FP32
-        float id = 1.0f / cb.det;
-        float Q0 = cb.c * id, Q1 = -cb.b * id, Q2 = cb.a * id;
+        // conic factor and half-plane terms, FP32
+        const float n0 = dot3(cb.P[0], cb.P[0]), n1 = dot3(cb.P[1], cb.P[1]);
+        float cr[3];
+        cross3(cb.P[0], cb.P[1], cr);
+        float det = dot3(cr, cr) + lp * (n0 + n1) + lp * lp;
+        float a_ = cb.a, b_ = cb.b, c_ = cb.c;
         float wpx = 0.0f, wpy = 0.0f;
         float nn = sqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
         int mode = MODE_HALF;
@@ -376,21 +406,21 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
             float u[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) u[k] = cb.L[0][k] * nh[0] + cb.L[1][k] * nh[1] + cb.L[2][k] * nh[2];
-            var_s = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            float k0 = cb.P[0][0] * u[0] + cb.P[0][1] * u[1] + cb.P[0][2] * u[2];
-            float k1 = cb.P[1][0] * u[0] + cb.P[1][1] * u[1] + cb.P[1][2] * u[2];
-            wx = Q0 * k0 + Q1 * k1;
-            wy = Q1 * k0 + Q2 * k1;
-            vv = var_s - (k0 * wx + k1 * wy);
+            var_s = dot3(u, u);
+            float k0 = dot3(cb.P[0], u), k1 = dot3(cb.P[1], u);
+            float id = 1.0f / det;
+            wx = (c_ * k0 - b_ * k1) * id;
+            wy = (a_ * k1 - b_ * k0) * id;
+            float up0[3], up1[3];
+            cross3(u, cb.P[0], up0);
+            cross3(u, cb.P[1], up1);
+            float trip = dot3(u, cr);
+            vv = (trip * trip + lp * (dot3(up0, up0) + dot3(up1, up1)) + lp * lp * var_s) * id;
             mode = (vv <= 1e-12f * var_s) ? MODE_STEP : MODE_NORMAL;
         }
-        bool degen = cb.det < kDetRelFp64 * cb.a * cb.c || (nn >= 1e-12f && vv < kVRelFp64 * var_s);
-        if (degen) {
+        if (mode == MODE_NORMAL && vv < kVRelFp64 * var_s) {
             Proj<double> d;
             d.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
-            if (d.det > 0.0) {
-                Q0 = (float)d.Q[0]; Q1 = (float)d.Q[1]; Q2 = (float)d.Q[2];
-            }
             mode = d.mode;
             if (mode == MODE_NORMAL) {
                 double sc = 1.0 / sqrt(2.0 * d.v);
@@ -404,6 +434,10 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
         } else if (mode == MODE_STEP) {
             wpx = wx * kStepScale; wpy = wy * kStepScale;
         }
+        // Cholesky factor of the conic
+        const float u22 = rsqrtf(c_);
+        const float u11 = sqrtf(c_ / det);
+        const float u12 = -b_ * rsqrtf(c_ * det);
 
         // SH colour
         if (!sh_loaded) {
@@ -439,8 +473,8 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
             rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
         }
         float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 3 * vi;
-        rec[0] = make_float4(cb.mux, cb.muy, Q0, Q1);
-        rec[1] = make_float4(Q2, wpx, wpy, o1);
+        rec[0] = make_float4(cb.mux, cb.muy, u11, u12);
+        rec[1] = make_float4(u22, wpx, wpy, o1);
         rec[2] = make_float4(o2, rgb[0], rgb[1], rgb[2]);
     }
 }

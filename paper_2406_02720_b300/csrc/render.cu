@@ -3,7 +3,7 @@
 // One thread block per tile (one thread per pixel).  The tile's depth-sorted
 // list is walked in batches that the block stages in shared memory.  For each
 // (pixel, splat) pair:
-//   d = p - mu-hat,  hat G = exp(-1/2 d^T conic d)             (Eq. 4-5)
+//   d = p - mu-hat,  hat G = exp(-1/2 |U d|^2), conic = U^T U  (Eq. 4-5)
 //   P = 1/2 erfc(-w'.d)                                         (Eq. 7-8)
 //   a = min(0.99, (alpha2 + (alpha1 - alpha2) P) hat G)          (Eq. 10)
 // composited front to back (Sec. 3.3).  A splat with a < 1/255 is skipped, and
@@ -13,7 +13,9 @@
 // erfc comes from Abramowitz & Stegun, Handbook of Mathematical Functions, 7.1.26
 // (|error| <= 1.5e-7 on erf), which needs exp(-z^2); the backward reuses that
 // exponential for dP/dz = exp(-z^2)/sqrt(pi).  Exponentials use the ex2.approx
-// instruction with the conic pre-scaled by log2(e).  Forward and backward
+// instruction with U pre-scaled by sqrt(log2(e)/2), so the exponent in base 2 is
+// -(s1^2 + s2^2) with (s1, s2) = U d: a sum of squares, accurate for thin
+// splats, never positive.  Forward and backward
 // evaluate the same inline function with explicit _rn intrinsics, so their
 // per-splat decisions are bit-identical.
 //
@@ -32,6 +34,8 @@ namespace hgs {
 namespace {
 
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kUScale = 0.84932180028801907f;   // sqrt(log2(e) / 2)
+constexpr float kInvUScale2 = 1.3862943611198906f; // 1 / kUScale^2 = 2 ln 2
 constexpr float kInvSqrtPi = 0.56418958354775628f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
@@ -61,16 +65,15 @@ __device__ __forceinline__ float lg2_approx(float x) {
 template <int BATCH>
 struct Batch {
     float mx[BATCH], my[BATCH];
-    float ha[BATCH], nb[BATCH], hc[BATCH];   // conic scaled by -log2(e)/2, -log2(e), -log2(e)/2
+    float u11[BATCH], u12[BATCH], u22[BATCH];  // Cholesky factor of the conic, scaled by kUScale
     float wx[BATCH], wy[BATCH];
     float a2[BATCH], da[BATCH];              // alpha2, alpha1 - alpha2
-    float cut[BATCH];                        // skip when the log2 exponent is below this
+    float qcut[BATCH];                       // skip when s1^2 + s2^2 exceeds this
     float r[BATCH], g[BATCH], b[BATCH];
 };
 
 template <int BATCH>
 struct BwdExtra {
-    float qa[BATCH], qb[BATCH], qc[BATCH];
     uint32_t id[BATCH];
 };
 
@@ -81,9 +84,9 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     const float4 r2 = __ldg(rec + 3 * (size_t)id + 2);
     s.mx[k] = r0.x;
     s.my[k] = r0.y;
-    s.ha[k] = __fmul_rn(-0.5f * kLog2e, r0.z);
-    s.nb[k] = __fmul_rn(-kLog2e, r0.w);
-    s.hc[k] = __fmul_rn(-0.5f * kLog2e, r1.x);
+    s.u11[k] = __fmul_rn(kUScale, r0.z);
+    s.u12[k] = __fmul_rn(kUScale, r0.w);
+    s.u22[k] = __fmul_rn(kUScale, r1.x);
     s.wx[k] = r1.y;
     s.wy[k] = r1.z;
     const float a1 = r1.w, a2 = r2.x;
@@ -91,14 +94,14 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     s.da[k] = __fsub_rn(a1, a2);
     const float amax = fmaxf(a1, a2);
     // alpha <= amax * G < 1/255 whenever log2 G < -log2(255 amax); 1e-3 covers ex2/lg2 error
-    s.cut[k] = amax > 0.0f ? __fsub_rn(-lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : __int_as_float(0x7f800000);
+    s.qcut[k] = amax > 0.0f ? __fadd_rn(lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : -1.0f;
     s.r[k] = r2.y;
     s.g[k] = r2.z;
     s.b[k] = r2.w;
 }
 
 struct Eval {
-    float a, G, P, A, dx, dy, e;
+    float a, G, P, A, dx, dy, e, s1, s2;
     bool clamped;
 };
 
@@ -108,10 +111,11 @@ template <int BATCH>
 __device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const Batch<BATCH> &s, int k, Eval &ev) {
     const float dx = __fsub_rn(fpx, s.mx[k]);
     const float dy = __fsub_rn(fpy, s.my[k]);
-    const float p2 = __fmaf_rn(dx, __fmaf_rn(s.ha[k], dx, __fmul_rn(s.nb[k], dy)),
-                               __fmul_rn(__fmul_rn(s.hc[k], dy), dy));
-    if (p2 > 0.0f || p2 < s.cut[k]) return false;
-    const float G = ex2_approx(p2);
+    const float s1 = __fmaf_rn(s.u11[k], dx, __fmul_rn(s.u12[k], dy));
+    const float s2 = __fmul_rn(s.u22[k], dy);
+    const float q = __fmaf_rn(s1, s1, __fmul_rn(s2, s2));
+    if (!(q <= s.qcut[k])) { ev.G = -1.0f; return false; }
+    const float G = ex2_approx(-q);
     const float z = __fmaf_rn(s.wx[k], dx, __fmul_rn(s.wy[k], dy));
     const float u = fabsf(z);
     const float t = rcp_approx(__fmaf_rn(kAsP, u, 1.0f));
@@ -127,8 +131,25 @@ __device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const Batch<BAT
     const float araw = __fmul_rn(A, G);
     ev.clamped = araw > kAlphaMax;
     ev.a = ev.clamped ? kAlphaMax : araw;
-    ev.G = G; ev.P = P; ev.A = A; ev.dx = dx; ev.dy = dy; ev.e = e;
+    ev.G = G; ev.P = P; ev.A = A; ev.dx = dx; ev.dy = dy; ev.e = e; ev.s1 = s1; ev.s2 = s2;
     return ev.a >= kAlphaMin;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+__device__ __forceinline__ void add_counters(unsigned long long *dst, unsigned long long a, unsigned long long b,
+                                             unsigned long long c, unsigned long long d) {
+    a = warp_sum_u64(a); b = warp_sum_u64(b); c = warp_sum_u64(c); d = warp_sum_u64(d);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(dst, a);
+        if (b) atomicAdd(dst + 1, b);
+        if (c) atomicAdd(dst + 2, c);
+        if (d) atomicAdd(dst + 3, d);
+    }
 }
 
 struct TileInfo {
@@ -158,7 +179,7 @@ __device__ __forceinline__ TileInfo tile_info(const RenderLaunch &p, int gtile) 
 }
 
 // ---- forward -------------------------------------------------------------------------
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, bool COUNT>
 __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s) {
     constexpr int NT = TW * TH;
     const int tid = threadIdx.x;
@@ -171,6 +192,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0;
     bool done = !inside;
+    unsigned long long c_visit = 0, c_full = 0, c_comp = 0;
     for (uint32_t base = ti.beg; base < ti.end; base += BATCH) {
         if (__syncthreads_count(done) == NT) break;
         for (int k = tid; k < BATCH; k += NT) {
@@ -186,9 +208,13 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
             const int cnt = (int)min((uint32_t)BATCH, ti.end - base);
             for (int k = 0; k < cnt; ++k) {
                 Eval ev;
-                if (!eval_alpha<BATCH>(fpx, fpy, s, k, ev)) continue;
+                if (COUNT) ++c_visit;
+                const bool hit = eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+                if (COUNT && ev.G >= 0.0f) ++c_full;
+                if (!hit) continue;
                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
                 if (Tn < kTMin) { done = true; break; }
+                if (COUNT) ++c_comp;
                 const float w = __fmul_rn(ev.a, T);
                 C0 = __fmaf_rn(s.r[k], w, C0);
                 C1 = __fmaf_rn(s.g[k], w, C1);
@@ -208,6 +234,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
         p.final_T[ti.pix_off + pix] = T;
         p.n_contrib[ti.pix_off + pix] = last;
     }
+    if (COUNT) add_counters(p.counters, c_visit, c_full, c_comp, 0ull);
 }
 
 // ---- backward ------------------------------------------------------------------------
@@ -217,7 +244,7 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, bool COUNT>
 __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s,
                                                 BwdExtra<BATCH> &x, uint32_t &s_maxlast) {
     constexpr int NT = TW * TH;
@@ -247,6 +274,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
     const float bgg = ti.bg[0] * g0 + ti.bg[1] * g1 + ti.bg[2] * g2;
     float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
     float4 *grad4 = reinterpret_cast<float4 *>(p.grad2d);
+    unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0;
     for (uint32_t bend = tile_end; bend > ti.beg;) {
         const uint32_t bstart = (bend - ti.beg > (uint32_t)BATCH) ? bend - BATCH : ti.beg;
         __syncthreads();
@@ -256,10 +284,6 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
                 stage<BATCH>(rec, id, s, k);
-                const float4 r0 = __ldg(rec + 3 * (size_t)id);
-                x.qa[k] = r0.z;
-                x.qb[k] = r0.w;
-                x.qc[k] = __ldg(rec + 3 * (size_t)id + 1).x;
                 x.id[k] = id;
             }
         }
@@ -268,7 +292,10 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
         for (int k = cnt - 1; k >= 0; --k) {
             const uint32_t pos = bstart + k - ti.beg;
             Eval ev;
-            bool contrib = inside && pos < last && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+            ev.G = -1.0f;
+            const bool cand = inside && pos < last;
+            bool contrib = cand && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+            if (COUNT) { c_visit += cand; c_full += (cand && ev.G >= 0.0f); c_contrib += contrib; }
             float gr[12];
 #pragma unroll
             for (int f = 0; f < 12; ++f) gr[f] = 0.0f;
@@ -292,8 +319,10 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                     gr[2] = -0.5f * dpow * dx * dx;
                     gr[3] = -dpow * dx * dy;
                     gr[4] = -0.5f * dpow * dy * dy;
-                    gr[0] = dpow * (x.qa[k] * dx + x.qb[k] * dy);
-                    gr[1] = dpow * (x.qb[k] * dx + x.qc[k] * dy);
+                    // d power / d mu-hat = conic d = U^T (U d)
+                    const float sc = dpow * kInvUScale2;
+                    gr[0] = sc * (s.u11[k] * ev.s1);
+                    gr[1] = sc * (s.u12[k] * ev.s1 + s.u22[k] * ev.s2);
                     if (fabsf(s.wx[k]) + fabsf(s.wy[k]) < kStepDetect) {
                         const float dz = dA * s.da[k] * ev.e * kInvSqrtPi;
                         gr[5] = dz * dx;
@@ -304,6 +333,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 }
             }
             const unsigned any = __ballot_sync(0xffffffffu, contrib);
+            if (COUNT && any && lane == 0) ++c_red;
             if (any) {
 #pragma unroll
                 for (int f = 0; f < 12; ++f) gr[f] = warp_sum(gr[f]);
@@ -317,6 +347,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
         }
         bend = bstart;
     }
+    if (COUNT) add_counters(p.counters + 3, c_visit, c_full, c_contrib, c_red);
 }
 
 // ---- kernels ------------------------------------------------------------------------
@@ -326,11 +357,11 @@ struct Queue {
     uint32_t bucket_cursor[33];
 };
 
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH) k_render_fwd(RenderLaunch p) {
     __shared__ Batch<BATCH> s;
     if (!p.cfg.persistent) {
-        render_tile_fwd<TW, TH, BATCH>(p, blockIdx.x, s);
+        render_tile_fwd<TW, TH, BATCH, COUNT>(p, blockIdx.x, s);
         return;
     }
     Queue *q = reinterpret_cast<Queue *>(p.ws);
@@ -341,18 +372,18 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(RenderLaunch p) {
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= (uint32_t)p.vt.total_tiles) break;
-        render_tile_fwd<TW, TH, BATCH>(p, (int)order[item], s);
+        render_tile_fwd<TW, TH, BATCH, COUNT>(p, (int)order[item], s);
         __syncthreads();
     }
 }
 
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH) k_render_bwd(RenderLaunch p) {
     __shared__ Batch<BATCH> s;
     __shared__ BwdExtra<BATCH> x;
     __shared__ uint32_t s_maxlast;
     if (!p.cfg.persistent) {
-        render_tile_bwd<TW, TH, BATCH>(p, blockIdx.x, s, x, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT>(p, blockIdx.x, s, x, s_maxlast);
         return;
     }
     Queue *q = reinterpret_cast<Queue *>(p.ws);
@@ -363,7 +394,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(RenderLaunch p) {
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= (uint32_t)p.vt.total_tiles) break;
-        render_tile_bwd<TW, TH, BATCH>(p, (int)order[item], s, x, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT>(p, (int)order[item], s, x, s_maxlast);
         __syncthreads();
     }
 }
@@ -400,36 +431,26 @@ __global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, 
     }
 }
 
-template <int TW, int TH, int BATCH>
-cudaError_t launch_fwd_t(const RenderLaunch &p, cudaStream_t s) {
+template <int TW, int TH, int BATCH, bool FWD, bool COUNT>
+cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
+    auto kern = FWD ? k_render_fwd<TW, TH, BATCH, COUNT> : k_render_bwd<TW, TH, BATCH, COUNT>;
     if (!p.cfg.persistent) {
-        k_render_fwd<TW, TH, BATCH><<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
+        kern<<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
         return cudaGetLastError();
     }
     static int blocks = 0;
     if (!blocks) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fwd<TW, TH, BATCH>, TW * TH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TW * TH, 0);
         blocks = num_sms() * std::max(occ, 1);
     }
-    k_render_fwd<TW, TH, BATCH><<<std::min(blocks, p.vt.total_tiles), TW * TH, 0, s>>>(p);
+    kern<<<std::min(blocks, p.vt.total_tiles), TW * TH, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int TW, int TH, int BATCH>
-cudaError_t launch_bwd_t(const RenderLaunch &p, cudaStream_t s) {
-    if (!p.cfg.persistent) {
-        k_render_bwd<TW, TH, BATCH><<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
-        return cudaGetLastError();
-    }
-    static int blocks = 0;
-    if (!blocks) {
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_bwd<TW, TH, BATCH>, TW * TH, 0);
-        blocks = num_sms() * std::max(occ, 1);
-    }
-    k_render_bwd<TW, TH, BATCH><<<std::min(blocks, p.vt.total_tiles), TW * TH, 0, s>>>(p);
-    return cudaGetLastError();
+template <int TW, int TH, int BATCH, bool FWD>
+cudaError_t launch_c(const RenderLaunch &p, cudaStream_t s) {
+    return p.counters ? launch_t<TW, TH, BATCH, FWD, true>(p, s) : launch_t<TW, TH, BATCH, FWD, false>(p, s);
 }
 
 cudaError_t prepare_queue(const RenderLaunch &p, cudaStream_t s) {
@@ -448,10 +469,10 @@ template <bool FWD, int TW, int TH>
 cudaError_t dispatch_batch(const RenderLaunch &p, cudaStream_t s) {
     const int batch = p.cfg.batch ? p.cfg.batch : TW * TH;
     switch (batch) {
-        case 32: return FWD ? launch_fwd_t<TW, TH, 32>(p, s) : launch_bwd_t<TW, TH, 32>(p, s);
-        case 64: return FWD ? launch_fwd_t<TW, TH, 64>(p, s) : launch_bwd_t<TW, TH, 64>(p, s);
-        case 128: return FWD ? launch_fwd_t<TW, TH, 128>(p, s) : launch_bwd_t<TW, TH, 128>(p, s);
-        case 256: return FWD ? launch_fwd_t<TW, TH, 256>(p, s) : launch_bwd_t<TW, TH, 256>(p, s);
+        case 32: return launch_c<TW, TH, 32, FWD>(p, s);
+        case 64: return launch_c<TW, TH, 64, FWD>(p, s);
+        case 128: return launch_c<TW, TH, 128, FWD>(p, s);
+        case 256: return launch_c<TW, TH, 256, FWD>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -90,6 +90,9 @@ def lib():
         L.hgs_project_bwd.restype = c_int
         L.hgs_project_bwd.argtypes = [POINTER(HgsGaussians), _CAM_P, vp, c_int, _CFG_P, vp,
                                       POINTER(HgsGaussianGrads), vp, vp]
+        L.hgs_render_stats.restype = c_int
+        L.hgs_render_stats.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp, c_size_t,
+                                       vp, vp, vp, vp, vp, vp, vp, vp]
         L.hgs_render_bwd.restype = c_int
         L.hgs_render_bwd.argtypes = [POINTER(HgsGaussians), POINTER(HgsProj), vp, vp, _CAM_P, vp, c_int,
                                      _CFG_P, vp, c_size_t, vp, vp, vp, vp, POINTER(HgsGaussianGrads), vp, vp]
@@ -170,6 +173,16 @@ def hgs_render_bwd(g, proj, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, 
     _check(lib().hgs_render_bwd(ctypes.byref(g), ctypes.byref(proj), ids, ranges, cams_host, cams_dev, n_views,
                                 ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, dL_dimage, grad2d,
                                 ctypes.byref(out), dev_status, stream), "hgs_render_bwd")
+
+
+def hgs_render_stats(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, image, final_T,
+                     n_contrib, dL_dimage, grad2d, counters, dev_status, stream):
+    _check(lib().hgs_render_stats(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
+                                  ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, dL_dimage, grad2d,
+                                  counters, dev_status, stream), "hgs_render_stats")
+
+
+STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd_contrib", "bwd_warp_red"]
 
 
 # ---- struct builders ----------------------------------------------------------------------

@@ -155,6 +155,17 @@ class Rasterizer:
         self.project_bwd(g, out)
         return out
 
+    def stats(self, dL_dimage: torch.Tensor) -> dict:
+        """Work counters of one forward + backward compositing pass (hgs_render_stats)."""
+        cnt = torch.zeros(8, dtype=torch.int64, device=self.device)
+        H.hgs_render_stats(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
+                           _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
+                           _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(dL_dimage),
+                           _vp(self.grad2d), _vp(cnt), _vp(self.status), self._stream())
+        self._raise_status(self.read_status())
+        v = cnt.cpu().tolist()
+        return {k: int(v[i]) for i, k in enumerate(H.STAT_NAMES)}
+
     def read_status(self) -> int:
         torch.cuda.current_stream(self.device).synchronize()
         return int(self.status.item())

@@ -4,10 +4,22 @@ import numpy as np
 
 import oracle
 
-# A pixel whose oracle decisions (1/255 floor, 1e-4 stop, step-mode sign) sit
-# within this relative distance of their threshold can flip between FP32 and FP64.
+# A pixel whose oracle decisions (1/255 floor, step-mode sign) sit within this
+# relative distance of their threshold can flip between FP32 and FP64.  The 1e-4
+# stop compares a transmittance that carries the rounding of every composited
+# splat, so its margin grows with their number.
 EXEMPT_MARGIN = 1e-4
+
+
+def exempt(ref):
+    """Pixels whose threshold decisions FP32 cannot be expected to reproduce."""
+    if "margin_a" not in ref:
+        return ref["margin"] <= EXEMPT_MARGIN
+    return (ref["margin_a"] <= EXEMPT_MARGIN) | (ref["margin_T"] <= EXEMPT_MARGIN * (1.0 + ref["n_comp"] / 100.0))
 IMAGE_ATOL = 1e-4
+# One threshold flip changes a pixel by at most about a/255-scale amounts; exempt
+# pixels must still agree to this bound.
+EXEMPT_ATOL = 2e-2
 
 
 def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persistent=False,
@@ -42,11 +54,16 @@ def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persi
     return out
 
 
-def compare_image(gpu_img, gpu_T, gpu_nc, ref, atol=IMAGE_ATOL, max_exempt_frac=1e-3):
-    """Max-abs image/T error on pixels away from threshold decisions; n_contrib equal there."""
-    ok = ref["margin"] > EXEMPT_MARGIN
+def compare_image(gpu_img, gpu_T, gpu_nc, ref, atol=IMAGE_ATOL, max_exempt_frac=1e-2):
+    """Max-abs image/T error on pixels away from threshold decisions; n_contrib equal there.
+    Pixels with a decision within EXEMPT_MARGIN of its threshold (long lists make
+    hundreds of decisions per pixel) are held to EXEMPT_ATOL only."""
+    ok = ~exempt(ref)
     n_ex = int((~ok).sum())
     assert n_ex <= max(4, max_exempt_frac * ok.size), f"{n_ex} exempt pixels of {ok.size}"
+    if n_ex:
+        ex_err = np.abs(gpu_img.astype(np.float64) - ref["image"])[:, ~ok]
+        assert ex_err.max() <= EXEMPT_ATOL, f"exempt pixel error {ex_err.max():.3g}"
     err = np.abs(gpu_img.astype(np.float64) - ref["image"])[:, ok]
     terr = np.abs(gpu_T.astype(np.float64) - ref["T"])[ok]
     assert err.size == 0 or err.max() <= atol, f"image max abs err {err.max():.3g}"
@@ -69,6 +86,6 @@ def masked_upstream(dL_list, refs):
     out = []
     for d, r in zip(dL_list, refs):
         d = np.array(d, np.float32, copy=True)
-        d[:, r["margin"] <= EXEMPT_MARGIN] = 0.0
+        d[:, exempt(r)] = 0.0
         out.append(d)
     return out
