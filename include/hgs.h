@@ -175,6 +175,27 @@ hgs_status hgs_bin(const hgs_proj *proj, int n, const hgs_camera *cams_host, int
                    uint64_t *keys_out, uint32_t *ids_out, uint32_t *ranges,
                    uint64_t *dev_num_pairs, int *dev_status, void *stream);
 
+/* Same as hgs_bin, but its scratch workspace is a fixed device array inside this
+ * library instead of caller memory; the paper has no counterpart (it is an
+ * interface for callers, not part of the method).  It is for callers that must
+ * not allocate device memory: plug-ins inside a host application that owns the
+ * device-memory budget, real-time loops that cannot afford a driver allocation
+ * (which may synchronise the device), and code enqueueing work while a stream is
+ * being captured, where allocation is not allowed.  The caller still provides
+ * every input and output; this call allocates nothing.
+ * Limit: hgs_bin_workspace_size(n, n_views, pair_capacity) must not exceed
+ * HGS_BIN_STATIC_SCRATCH_BYTES (32 MiB, held on every GPU that loads the library
+ * until the process exits), else HGS_ERR_CAPACITY and nothing is enqueued.
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (different streams or threads)
+ * race; calls in order on one stream are safe.  Errors otherwise as hgs_bin. */
+#define HGS_BIN_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+hgs_status hgs_bin_static(const hgs_proj *proj, int n, const hgs_camera *cams_host, int n_views,
+                          const hgs_config *cfg, size_t pair_capacity, uint64_t *keys_out,
+                          uint32_t *ids_out, uint32_t *ranges, uint64_t *dev_num_pairs,
+                          int *dev_status, void *stream);
+
 /* ---- A6: forward compositing ----------------------------------------------- */
 
 /* Per pixel, front to back over its tile's sorted list (Sec. 3.3 blending with

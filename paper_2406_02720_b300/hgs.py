@@ -81,6 +81,9 @@ def lib():
         L.hgs_bin.restype = c_int
         L.hgs_bin.argtypes = [POINTER(HgsProj), c_int, _CAM_P, c_int, _CFG_P, vp, c_size_t, c_size_t,
                               vp, vp, vp, vp, vp, vp]
+        L.hgs_bin_static.restype = c_int
+        L.hgs_bin_static.argtypes = [POINTER(HgsProj), c_int, _CAM_P, c_int, _CFG_P, c_size_t, vp, vp, vp, vp, vp,
+                                     vp]
         L.hgs_render_fwd.restype = c_int
         L.hgs_render_fwd.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp,
                                      c_size_t, vp, vp, vp, vp, vp]
@@ -147,6 +150,17 @@ def hgs_bin(proj, n, cams_host, n_views, cfg, ws, ws_bytes, pair_capacity, keys_
             dev_num_pairs, dev_status, stream):
     _check(lib().hgs_bin(ctypes.byref(proj), n, cams_host, n_views, ctypes.byref(cfg), ws, ws_bytes,
                          pair_capacity, keys_out, ids_out, ranges, dev_num_pairs, dev_status, stream), "hgs_bin")
+
+
+HGS_BIN_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def hgs_bin_static(proj, n, cams_host, n_views, cfg, pair_capacity, keys_out, ids_out, ranges, dev_num_pairs,
+                   dev_status, stream):
+    """hgs_bin with the scratch workspace in the library's fixed device array (no
+    allocation by the caller or the call)."""
+    _check(lib().hgs_bin_static(ctypes.byref(proj), n, cams_host, n_views, ctypes.byref(cfg), pair_capacity,
+                                keys_out, ids_out, ranges, dev_num_pairs, dev_status, stream), "hgs_bin_static")
 
 
 def hgs_render_fwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, image, final_T,
