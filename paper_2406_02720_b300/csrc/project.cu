@@ -29,7 +29,7 @@
 namespace hgs {
 namespace {
 
-constexpr int kProjBlock = 256;
+constexpr int kProjBlock = 128;
 enum { MODE_CULLED = 0, MODE_NORMAL = 1, MODE_STEP = 2, MODE_HALF = 3 };
 
 // Degeneracy test that sends a splat's half-plane terms to the FP64 path: the
@@ -310,30 +310,27 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     Y[15] = -kC3a * x * (xx - 3.0f * yy);
 }
 
-// Cartesian gradient of each basis polynomial.
-__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float dY[16][3]) {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) dY[i][0] = dY[i][1] = dY[i][2] = 0.0f;
+// sum_l w_l grad Y_l, with the Cartesian gradient of each basis polynomial.
+__device__ __forceinline__ void sh_grad_dot(int deg, float x, float y, float z, const float w[16], float gd[3]) {
+    gd[0] = gd[1] = gd[2] = 0.0f;
     if (deg < 1) return;
-    dY[1][1] = -kC1; dY[2][2] = kC1; dY[3][0] = -kC1;
+    gd[0] -= kC1 * w[3];
+    gd[1] -= kC1 * w[1];
+    gd[2] += kC1 * w[2];
     if (deg < 2) return;
-    float xx = x * x, yy = y * y, zz = z * z;
-    dY[4][0] = kC2a * y; dY[4][1] = kC2a * x;
-    dY[5][1] = -kC2a * z; dY[5][2] = -kC2a * y;
-    dY[6][0] = -2.0f * kC2b * x; dY[6][1] = -2.0f * kC2b * y; dY[6][2] = 4.0f * kC2b * z;
-    dY[7][0] = -kC2a * z; dY[7][2] = -kC2a * x;
-    dY[8][0] = 2.0f * kC2c * x; dY[8][1] = -2.0f * kC2c * y;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gd[0] += kC2a * (y * w[4] - z * w[7]) - 2.0f * kC2b * x * w[6] + 2.0f * kC2c * x * w[8];
+    gd[1] += kC2a * (x * w[4] - z * w[5]) - 2.0f * kC2b * y * w[6] - 2.0f * kC2c * y * w[8];
+    gd[2] += -kC2a * (y * w[5] + x * w[7]) + 4.0f * kC2b * z * w[6];
     if (deg < 3) return;
-    dY[9][0] = -kC3a * 6.0f * x * y; dY[9][1] = -kC3a * 3.0f * (xx - yy);
-    dY[10][0] = kC3b * y * z; dY[10][1] = kC3b * x * z; dY[10][2] = kC3b * x * y;
-    dY[11][0] = 2.0f * kC3c * x * y; dY[11][1] = -kC3c * (4.0f * zz - xx - 3.0f * yy);
-    dY[11][2] = -8.0f * kC3c * y * z;
-    dY[12][0] = -6.0f * kC3d * x * z; dY[12][1] = -6.0f * kC3d * y * z;
-    dY[12][2] = kC3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
-    dY[13][0] = -kC3c * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * kC3c * x * y;
-    dY[13][2] = -8.0f * kC3c * x * z;
-    dY[14][0] = 2.0f * kC3e * x * z; dY[14][1] = -2.0f * kC3e * y * z; dY[14][2] = kC3e * (xx - yy);
-    dY[15][0] = -3.0f * kC3a * (xx - yy); dY[15][1] = 6.0f * kC3a * x * y;
+    gd[0] += -6.0f * kC3a * x * y * w[9] + kC3b * y * z * w[10] + 2.0f * kC3c * x * y * w[11]
+             - 6.0f * kC3d * x * z * w[12] - kC3c * (4.0f * zz - 3.0f * xx - yy) * w[13]
+             + 2.0f * kC3e * x * z * w[14] - 3.0f * kC3a * (xx - yy) * w[15];
+    gd[1] += -3.0f * kC3a * (xx - yy) * w[9] + kC3b * x * z * w[10] - kC3c * (4.0f * zz - xx - 3.0f * yy) * w[11]
+             - 6.0f * kC3d * y * z * w[12] + 2.0f * kC3c * x * y * w[13] - 2.0f * kC3e * y * z * w[14]
+             + 6.0f * kC3a * x * y * w[15];
+    gd[2] += kC3b * x * y * w[10] - 8.0f * kC3c * y * z * w[11] + kC3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12]
+             - 8.0f * kC3c * x * z * w[13] + kC3e * (xx - yy) * w[14];
 }
 
 __device__ __forceinline__ void camera_centre(const hgs_camera &cam, float c[3]) {
@@ -342,49 +339,139 @@ __device__ __forceinline__ void camera_centre(const hgs_camera &cam, float c[3])
     for (int i = 0; i < 3; ++i) c[i] = -(V[i] * V[3] + V[4 + i] * V[7] + V[8 + i] * V[11]);
 }
 
-// Coalesced float4 staging of a [n,3] array slice into shared memory.
-__device__ __forceinline__ void stage3(const float *__restrict__ src, int n, int base, float *dst) {
-    int cnt = 3 * min(kProjBlock, n - base);
-    const float *s = src + 3 * (size_t)base;
-    int n4 = cnt >> 2;
-    for (int j = threadIdx.x; j < n4; j += blockDim.x)
-        reinterpret_cast<float4 *>(dst)[j] = __ldg(reinterpret_cast<const float4 *>(s) + j);
-    for (int j = 4 * n4 + threadIdx.x; j < cnt; j += blockDim.x) dst[j] = __ldg(s + j);
+// ---- parameter staging -----------------------------------------------------------
+// A block projects kProjBlock consecutive splats.  Their parameter rows are
+// contiguous in every input array, so the block copies each slice into shared
+// memory with 16-byte cp.async copies (bypassing registers), then each thread
+// reads its own row.  SH rows of 48 floats are padded to 52 in shared memory so
+// that 128-bit reads of consecutive threads fall in distinct banks.
+constexpr int kShStride3 = 52;
+
+__device__ __forceinline__ int sh_stride(int deg) { return deg == 3 ? kShStride3 : 3 * (deg + 1) * (deg + 1); }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// rows x row_floats floats from src (16-B aligned) into dst with the given row stride.
+__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int rows, int row_floats, float *dst,
+                                           int dst_stride) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (row_floats == dst_stride) {
+        const int cnt = rows * row_floats, n4 = cnt >> 2;
+        for (int j = tid; j < n4; j += nt) cp_async16(dst + 4 * j, src + 4 * j);
+        for (int j = 4 * n4 + tid; j < cnt; j += nt) dst[j] = __ldg(src + j);
+    } else {                                   // row_floats is a multiple of 4
+        const int per = row_floats >> 2, n4 = rows * per;
+        for (int j = tid; j < n4; j += nt) {
+            const int r = j / per, c = j - r * per;
+            cp_async16(dst + r * dst_stride + 4 * c, src + (size_t)r * row_floats + 4 * c);
+        }
+    }
 }
 
-__global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
-    __shared__ __align__(16) float s_mean[3 * kProjBlock];
-    __shared__ __align__(16) float s_scale[3 * kProjBlock];
-    __shared__ __align__(16) float s_nrm[3 * kProjBlock];
-    const int n = p.g.n;
-    const int base = blockIdx.x * kProjBlock;
-    stage3(p.g.means, n, base, s_mean);
-    stage3(p.g.scales, n, base, s_scale);
-    stage3(p.g.normals, n, base, s_nrm);
+struct StageSmem {
+    float mean[3 * kProjBlock];
+    float scale[3 * kProjBlock];
+    float nrm[3 * kProjBlock];
+    float quat[4 * kProjBlock];
+    float o1[kProjBlock];
+    float o2[kProjBlock];
+    float sh[kShStride3 * kProjBlock];
+};
+
+__device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, int rows, StageSmem &sm) {
+    const int deg = g.sh_degree, nc3 = 3 * (deg + 1) * (deg + 1);
+    stage_rows(g.means + 3 * (size_t)base, rows, 3, sm.mean, 3);
+    stage_rows(g.scales + 3 * (size_t)base, rows, 3, sm.scale, 3);
+    stage_rows(g.normals + 3 * (size_t)base, rows, 3, sm.nrm, 3);
+    stage_rows(g.quats + 4 * (size_t)base, rows, 4, sm.quat, 4);
+    stage_rows(g.opac1 + base, rows, 1, sm.o1, 1);
+    stage_rows(g.opac2 + base, rows, 1, sm.o2, 1);
+    stage_rows(g.sh + (size_t)nc3 * base, rows, nc3, sm.sh, sh_stride(deg));
+    cp_async_wait_all();
     __syncthreads();
-    const int i = base + threadIdx.x;
-    if (i >= n) return;
-    float m[3], s[3], nrm[3], q[4];
+}
+
+struct Params {
+    float m[3], s[3], q[4], n[3];
+};
+
+__device__ __forceinline__ Params read_params(const StageSmem &sm, int t) {
+    Params P;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        m[k] = s_mean[3 * threadIdx.x + k];
-        s[k] = s_scale[3 * threadIdx.x + k];
-        nrm[k] = s_nrm[3 * threadIdx.x + k];
+        P.m[k] = sm.mean[3 * t + k];
+        P.s[k] = sm.scale[3 * t + k];
+        P.n[k] = sm.nrm[3 * t + k];
     }
-    float4 q4 = __ldg(reinterpret_cast<const float4 *>(p.g.quats) + i);
-    q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
-    const float o1 = __ldg(p.g.opac1 + i), o2 = __ldg(p.g.opac2 + i);
-    const int deg = p.g.sh_degree;
+    const float4 q4 = reinterpret_cast<const float4 *>(sm.quat)[t];
+    P.q[0] = q4.x; P.q[1] = q4.y; P.q[2] = q4.z; P.q[3] = q4.w;
+    return P;
+}
+
+// SH colour (before the clamp) from the staged coefficients of thread t.
+__device__ __forceinline__ void sh_colour(const StageSmem &sm, int t, int deg, const float Y[16], float out[3]) {
+    const float *c = sm.sh + t * sh_stride(deg);
     const int nc = (deg + 1) * (deg + 1);
-    float sh[48];
-    bool sh_loaded = false;
+    float r = 0.0f, g = 0.0f, b = 0.0f;
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        if (l < nc) {
+            r += c[3 * l] * Y[l];
+            g += c[3 * l + 1] * Y[l];
+            b += c[3 * l + 2] * Y[l];
+        }
+    }
+    out[0] = r + 0.5f; out[1] = g + 0.5f; out[2] = b + 0.5f;
+}
+
+struct HalfPlane {
+    int mode;
+    float wpx, wpy;
+};
+
+// FP64 recomputation of the half-plane terms of a splat whose plane nearly
+// contains the ray (rare; kept out of line so the FP32 path keeps its registers).
+__device__ __noinline__ HalfPlane half_plane_fp64(Params P, const hgs_camera &cam, float lp, int fov_clamp) {
+    Proj<double> d;
+    d.run(P.m, P.s, P.q, P.n, cam, lp, fov_clamp);
+    HalfPlane h;
+    h.mode = d.mode;
+    h.wpx = h.wpy = 0.0f;
+    if (d.mode == MODE_NORMAL) {
+        const double sc = 1.0 / sqrt(2.0 * d.v);
+        h.wpx = (float)(d.w[0] * sc);
+        h.wpy = (float)(d.w[1] * sc);
+    } else if (d.mode == MODE_STEP) {
+        h.wpx = (float)d.w[0] * kStepScale;
+        h.wpy = (float)d.w[1] * kStepScale;
+    }
+    return h;
+}
+
+__global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StageSmem &sm = *reinterpret_cast<StageSmem *>(smem_raw);
+    const int n = p.g.n;
+    const int base = blockIdx.x * kProjBlock;
+    const int rows = min(kProjBlock, n - base);
+    stage_params(p.g, base, rows, sm);
+    const int t = threadIdx.x;
+    if (t >= rows) return;
+    const int i = base + t;
+    const Params P = read_params(sm, t);
+    const float o1 = sm.o1[t], o2 = sm.o2[t];
+    const int deg = p.g.sh_degree;
     const float lp = p.cfg.lowpass;
 
     for (int v = 0; v < p.n_views; ++v) {
         const hgs_camera &cam = p.cams[v];
         const size_t vi = (size_t)v * n + i;
         Canon cb;
-        canon_project(m, s, q, cam, lp, p.cfg.fov_clamp, p.cfg.tile_w, p.cfg.tile_h, cb);
+        canon_project(P.m, P.s, P.q, cam, lp, p.cfg.fov_clamp, p.cfg.tile_w, p.cfg.tile_h, cb);
         p.out.depth[vi] = cb.depth;
         reinterpret_cast<int4 *>(p.out.rect)[vi] = make_int4(cb.rect[0], cb.rect[1], cb.rect[2], cb.rect[3]);
         p.out.tiles[vi] = cb.culled ? 0u : cb.tiles;
@@ -394,45 +481,36 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
         const float n0 = dot3(cb.P[0], cb.P[0]), n1 = dot3(cb.P[1], cb.P[1]);
         float cr[3];
         cross3(cb.P[0], cb.P[1], cr);
-        float det = dot3(cr, cr) + lp * (n0 + n1) + lp * lp;
-        float a_ = cb.a, b_ = cb.b, c_ = cb.c;
-        float wpx = 0.0f, wpy = 0.0f;
-        float nn = sqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-        int mode = MODE_HALF;
-        float wx = 0, wy = 0, vv = 0, var_s = 0;
+        const float det = dot3(cr, cr) + lp * (n0 + n1) + lp * lp;
+        const float a_ = cb.a, b_ = cb.b, c_ = cb.c;
+        HalfPlane h;
+        h.mode = MODE_HALF;
+        h.wpx = h.wpy = 0.0f;
+        const float nn = sqrtf(dot3(P.n, P.n));
         if (nn >= 1e-12f) {
-            float in = 1.0f / nn;
-            float nh[3] = {nrm[0] * in, nrm[1] * in, nrm[2] * in};
+            const float in = 1.0f / nn;
+            const float nh[3] = {P.n[0] * in, P.n[1] * in, P.n[2] * in};
             float u[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) u[k] = cb.L[0][k] * nh[0] + cb.L[1][k] * nh[1] + cb.L[2][k] * nh[2];
-            var_s = dot3(u, u);
-            float k0 = dot3(cb.P[0], u), k1 = dot3(cb.P[1], u);
-            float id = 1.0f / det;
-            wx = (c_ * k0 - b_ * k1) * id;
-            wy = (a_ * k1 - b_ * k0) * id;
+            const float var_s = dot3(u, u);
+            const float k0 = dot3(cb.P[0], u), k1 = dot3(cb.P[1], u);
+            const float id = 1.0f / det;
+            const float wx = (c_ * k0 - b_ * k1) * id;
+            const float wy = (a_ * k1 - b_ * k0) * id;
             float up0[3], up1[3];
             cross3(u, cb.P[0], up0);
             cross3(u, cb.P[1], up1);
-            float trip = dot3(u, cr);
-            vv = (trip * trip + lp * (dot3(up0, up0) + dot3(up1, up1)) + lp * lp * var_s) * id;
-            mode = (vv <= 1e-12f * var_s) ? MODE_STEP : MODE_NORMAL;
-        }
-        if (mode == MODE_NORMAL && vv < kVRelFp64 * var_s) {
-            Proj<double> d;
-            d.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
-            mode = d.mode;
-            if (mode == MODE_NORMAL) {
-                double sc = 1.0 / sqrt(2.0 * d.v);
-                wpx = (float)(d.w[0] * sc); wpy = (float)(d.w[1] * sc);
-            } else if (mode == MODE_STEP) {
-                wpx = (float)d.w[0] * kStepScale; wpy = (float)d.w[1] * kStepScale;
+            const float trip = dot3(u, cr);
+            const float vv = (trip * trip + lp * (dot3(up0, up0) + dot3(up1, up1)) + lp * lp * var_s) * id;
+            if (vv < kVRelFp64 * var_s) {
+                h = half_plane_fp64(P, cam, lp, p.cfg.fov_clamp);
+            } else {
+                const float sc = rsqrtf(2.0f * vv);
+                h.mode = MODE_NORMAL;
+                h.wpx = wx * sc;
+                h.wpy = wy * sc;
             }
-        } else if (mode == MODE_NORMAL) {
-            float sc = rsqrtf(2.0f * vv);
-            wpx = wx * sc; wpy = wy * sc;
-        } else if (mode == MODE_STEP) {
-            wpx = wx * kStepScale; wpy = wy * kStepScale;
         }
         // Cholesky factor of the conic
         const float u22 = rsqrtf(c_);
@@ -440,46 +518,26 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ProjLaunch p) {
         const float u12 = -b_ * rsqrtf(c_ * det);
 
         // SH colour
-        if (!sh_loaded) {
-            const float4 *sp = reinterpret_cast<const float4 *>(p.g.sh + (size_t)i * nc * 3);
-            int n4 = (nc * 3) >> 2;
-            if (((nc * 3) & 3) == 0 && ((reinterpret_cast<uintptr_t>(sp) & 15) == 0)) {
-#pragma unroll
-                for (int j = 0; j < 12; ++j)
-                    if (j < n4) {
-                        float4 t4 = __ldg(sp + j);
-                        sh[4 * j] = t4.x; sh[4 * j + 1] = t4.y; sh[4 * j + 2] = t4.z; sh[4 * j + 3] = t4.w;
-                    }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 48; ++j)
-                    if (j < nc * 3) sh[j] = __ldg(p.g.sh + (size_t)i * nc * 3 + j);
-            }
-            sh_loaded = true;
-        }
         float cpos[3];
         camera_centre(cam, cpos);
-        float dx = m[0] - cpos[0], dy = m[1] - cpos[1], dz = m[2] - cpos[2];
-        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        const float dx = P.m[0] - cpos[0], dy = P.m[1] - cpos[1], dz = P.m[2] - cpos[2];
+        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
         sh_basis(deg, dx * il, dy * il, dz * il, Y);
         float rgb[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int l = 0; l < 16; ++l)
-                if (l < nc) acc += sh[3 * l + ch] * Y[l];
-            rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
-        }
+        sh_colour(sm, t, deg, Y, rgb);
         float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 3 * vi;
         rec[0] = make_float4(cb.mux, cb.muy, u11, u12);
-        rec[1] = make_float4(u22, wpx, wpy, o1);
-        rec[2] = make_float4(o2, rgb[0], rgb[1], rgb[2]);
+        rec[1] = make_float4(u22, h.wpx, h.wpy, o1);
+        rec[2] = make_float4(o2, fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f));
     }
 }
 
 // ---- adjoint -------------------------------------------------------------------
+struct G2 {
+    float v[12];
+};
+
 template <typename T>
 __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const hgs_camera &cam,
                                          const float *g2, float gm[3], float gs[3], float gq[4],
@@ -579,117 +637,146 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
     for (int j = 0; j < 3; ++j) gm[j] += (float)(V[j] * gt[0] + V[4 + j] * gt[1] + V[8 + j] * gt[2]);
 }
 
-__global__ void __launch_bounds__(kProjBlock) k_project_bwd(ProjBwdLaunch p) {
-    const int n = p.g.n;
-    const int i = blockIdx.x * kProjBlock + threadIdx.x;
-    if (i >= n) return;
-    float m[3], s[3], nrm[3], q[4];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        m[k] = __ldg(p.g.means + 3 * (size_t)i + k);
-        s[k] = __ldg(p.g.scales + 3 * (size_t)i + k);
-        nrm[k] = __ldg(p.g.normals + 3 * (size_t)i + k);
-    }
-    float4 q4 = __ldg(reinterpret_cast<const float4 *>(p.g.quats) + i);
-    q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
-    const int deg = p.g.sh_degree;
-    const int nc = (deg + 1) * (deg + 1);
-    float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gn[3] = {0, 0, 0};
-    float go1 = 0, go2 = 0;
-    float gsh[48];
-#pragma unroll
-    for (int j = 0; j < 48; ++j) gsh[j] = 0.0f;
-    float sh[48];
-    bool sh_loaded = false;
-    const float lp = p.cfg.lowpass;
+struct Grads {
+    float m[3], s[3], q[4], n[3];
+};
 
-    for (int v = 0; v < p.n_views; ++v) {
-        const size_t vi = (size_t)v * n + i;
-        const float4 *g4 = reinterpret_cast<const float4 *>(p.grad2d) + 3 * vi;
-        float4 a = g4[0], b = g4[1], c = g4[2];
-        float g2[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        bool any = false;
+// FP64 adjoint of the projection of one near-degenerate splat (rare, out of line).
+__device__ __noinline__ Grads proj_vjp_fp64(Params P, const hgs_camera &cam, float lp, int fov_clamp, G2 g2) {
+    Proj<double> d;
+    d.run(P.m, P.s, P.q, P.n, cam, lp, fov_clamp);
+    Grads r;
 #pragma unroll
-        for (int j = 0; j < 12; ++j) any |= (g2[j] != 0.0f);
-        if (!any) continue;
-        const hgs_camera &cam = p.cams[v];
-        go1 += g2[7];
-        go2 += g2[8];
-        Proj<float> f;
-        f.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
-        if (f.degenerate()) {
-            Proj<double> d;
-            d.run(m, s, q, nrm, cam, lp, p.cfg.fov_clamp);
-            proj_vjp<double>(d, s, cam, g2, gm, gs, gq, gn);
-        } else {
-            proj_vjp<float>(f, s, cam, g2, gm, gs, gq, gn);
-        }
-        // SH colour
-        if (!sh_loaded) {
+    for (int k = 0; k < 3; ++k) r.m[k] = r.s[k] = r.n[k] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 48; ++j)
-                if (j < nc * 3) sh[j] = __ldg(p.g.sh + (size_t)i * nc * 3 + j);
-            sh_loaded = true;
-        }
-        float cpos[3];
-        camera_centre(cam, cpos);
-        float dv[3] = {m[0] - cpos[0], m[1] - cpos[1], m[2] - cpos[2]};
-        float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-        float dir[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
-        float Y[16], dY[16][3];
-        sh_basis(deg, dir[0], dir[1], dir[2], Y);
-        sh_basis_grad(deg, dir[0], dir[1], dir[2], dY);
-        float graw[3];
+    for (int k = 0; k < 4; ++k) r.q[k] = 0.0f;
+    proj_vjp<double>(d, P.s, cam, g2.v, r.m, r.s, r.q, r.n);
+    return r;
+}
+
+__global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StageSmem &sm = *reinterpret_cast<StageSmem *>(smem_raw);
+    float *gsh_s = reinterpret_cast<float *>(smem_raw + sizeof(StageSmem));   // [kProjBlock][stride]
+    const int n = p.g.n;
+    const int base = blockIdx.x * kProjBlock;
+    const int rows = min(kProjBlock, n - base);
+    const int deg = p.g.sh_degree;
+    const int nc = (deg + 1) * (deg + 1), nc3 = 3 * nc, shs = sh_stride(deg);
+    for (int j = threadIdx.x; j < kProjBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
+    stage_params(p.g, base, rows, sm);
+    const int t = threadIdx.x;
+    const float lp = p.cfg.lowpass;
+    float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gn[3] = {0, 0, 0};
+    float go1 = 0.0f, go2 = 0.0f;
+    if (t < rows) {
+        const int i = base + t;
+        const Params P = read_params(sm, t);
+        float *gsh = gsh_s + t * shs;
+        const float *shc = sm.sh + t * shs;
+        for (int v = 0; v < p.n_views; ++v) {
+            const size_t vi = (size_t)v * n + i;
+            const float4 *g4 = reinterpret_cast<const float4 *>(p.grad2d) + 3 * vi;
+            const float4 a = g4[0], b = g4[1], c = g4[2];
+            G2 g2;
+            g2.v[0] = a.x; g2.v[1] = a.y; g2.v[2] = a.z; g2.v[3] = a.w;
+            g2.v[4] = b.x; g2.v[5] = b.y; g2.v[6] = b.z; g2.v[7] = b.w;
+            g2.v[8] = c.x; g2.v[9] = c.y; g2.v[10] = c.z; g2.v[11] = c.w;
+            bool any = false;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.0f;
+            for (int j = 0; j < 12; ++j) any |= (g2.v[j] != 0.0f);
+            if (!any) continue;
+            const hgs_camera &cam = p.cams[v];
+            go1 += g2.v[7];
+            go2 += g2.v[8];
+            Proj<float> f;
+            f.run(P.m, P.s, P.q, P.n, cam, lp, p.cfg.fov_clamp);
+            if (f.degenerate()) {
+                const Grads r = proj_vjp_fp64(P, cam, lp, p.cfg.fov_clamp, g2);
 #pragma unroll
-            for (int l = 0; l < 16; ++l)
-                if (l < nc) acc += sh[3 * l + ch] * Y[l];
-            graw[ch] = (acc + 0.5f < 0.0f) ? 0.0f : g2[9 + ch];
-        }
-        float gd[3] = {0, 0, 0};
+                for (int k = 0; k < 3; ++k) { gm[k] += r.m[k]; gs[k] += r.s[k]; gn[k] += r.n[k]; }
 #pragma unroll
-        for (int l = 0; l < 16; ++l) {
-            if (l >= nc) break;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                gsh[3 * l + ch] += graw[ch] * Y[l];
-                float cg = graw[ch] * sh[3 * l + ch];
-                gd[0] += cg * dY[l][0]; gd[1] += cg * dY[l][1]; gd[2] += cg * dY[l][2];
+                for (int k = 0; k < 4; ++k) gq[k] += r.q[k];
+            } else {
+                proj_vjp<float>(f, P.s, cam, g2.v, gm, gs, gq, gn);
             }
+            // SH colour: rgb = max(0, sum c Y(dir) + 1/2), dir = unit(mu - camera centre)
+            float cpos[3];
+            camera_centre(cam, cpos);
+            const float dv[3] = {P.m[0] - cpos[0], P.m[1] - cpos[1], P.m[2] - cpos[2]};
+            const float il = rsqrtf(dot3(dv, dv));
+            const float dir[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
+            float Y[16];
+            sh_basis(deg, dir[0], dir[1], dir[2], Y);
+            float raw[3];
+            sh_colour(sm, t, deg, Y, raw);
+            float graw[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) graw[ch] = raw[ch] < 0.0f ? 0.0f : g2.v[9 + ch];
+            float wl[16];
+#pragma unroll
+            for (int l = 0; l < 16; ++l) {
+                wl[l] = 0.0f;
+                if (l < nc) {
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        gsh[3 * l + ch] += graw[ch] * Y[l];
+                        wl[l] += graw[ch] * shc[3 * l + ch];
+                    }
+                }
+            }
+            float gd[3];
+            sh_grad_dot(deg, dir[0], dir[1], dir[2], wl, gd);
+            const float dd = dot3(gd, dir);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gm[k] += (gd[k] - dd * dir[k]) * il;
         }
-        float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) gm[k] += (gd[k] - dd * dir[k]) * il;
+        for (int k = 0; k < 3; ++k) {
+            p.out.means[3 * (size_t)i + k] = gm[k];
+            p.out.scales[3 * (size_t)i + k] = gs[k];
+            p.out.normals[3 * (size_t)i + k] = gn[k];
+        }
+        reinterpret_cast<float4 *>(p.out.quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        p.out.opac1[i] = go1;
+        p.out.opac2[i] = go2;
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        p.out.means[3 * (size_t)i + k] = gm[k];
-        p.out.scales[3 * (size_t)i + k] = gs[k];
-        p.out.normals[3 * (size_t)i + k] = gn[k];
+    __syncthreads();
+    // SH gradients: shared rows -> contiguous global slice, coalesced
+    float *dst = p.out.sh + (size_t)nc3 * base;
+    for (int j = threadIdx.x; j < rows * nc3; j += blockDim.x) {
+        const int r = j / nc3, c = j - r * nc3;
+        dst[j] = gsh_s[r * shs + c];
     }
-    reinterpret_cast<float4 *>(p.out.quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-    p.out.opac1[i] = go1;
-    p.out.opac2[i] = go2;
-#pragma unroll
-    for (int j = 0; j < 48; ++j)
-        if (j < nc * 3) p.out.sh[(size_t)i * nc * 3 + j] = gsh[j];
 }
 
 }  // namespace
 
+size_t project_smem_bytes(bool bwd) {
+    return sizeof(StageSmem) + (bwd ? sizeof(float) * kShStride3 * kProjBlock : 0);
+}
+
 cudaError_t launch_project(const ProjLaunch &p, cudaStream_t s) {
     if (p.g.n == 0) return cudaSuccess;
-    dim3 grid(div_up(p.g.n, kProjBlock));
-    k_project<<<grid, kProjBlock, 0, s>>>(p);
+    static bool attr = false;
+    const size_t smem = project_smem_bytes(false);
+    if (!attr) {
+        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_project<<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project_bwd(const ProjBwdLaunch &p, cudaStream_t s) {
     if (p.g.n == 0) return cudaSuccess;
-    dim3 grid(div_up(p.g.n, kProjBlock));
-    k_project_bwd<<<grid, kProjBlock, 0, s>>>(p);
+    static bool attr = false;
+    const size_t smem = project_smem_bytes(true);
+    if (!attr) {
+        cudaFuncSetAttribute(k_project_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_project_bwd<<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -19,10 +19,18 @@
 // evaluate the same inline function with explicit _rn intrinsics, so their
 // per-splat decisions are bit-identical.
 //
+// Each warp owns an 8x4 block of the tile's pixels.  Per 32 staged splats it
+// tests the bounding box of every splat's cut-off ellipse (the pixels where
+// alpha could reach 1/255) against its block and ballots; only the hits are
+// visited.  The box is inflated past the cut-off, so culling changes no
+// per-pixel decision.
+//
 // The backward walks each pixel's list back to front from its last composited
-// splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i),
-// reduces the 12 screen-space gradients over the warp and issues three float4
-// atomics per (warp, splat).
+// splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i).
+// The 12 screen-space gradients of a (warp, splat) are summed with a butterfly
+// that halves the number of live values at each of its first four levels (16
+// shuffles instead of 60) and land with one 12-lane atomic instruction; a splat
+// that only one lane of the warp touches goes straight to three float4 atomics.
 //
 // Persistent mode: a grid of resident blocks pops global tile ids from an
 // atomic queue whose order is heaviest-first (bucketed by list length).
@@ -70,10 +78,7 @@ struct Batch {
     float a2[BATCH], da[BATCH];              // alpha2, alpha1 - alpha2
     float qcut[BATCH];                       // skip when s1^2 + s2^2 exceeds this
     float r[BATCH], g[BATCH], b[BATCH];
-};
-
-template <int BATCH>
-struct BwdExtra {
+    float bxl[BATCH], bxh[BATCH], byl[BATCH], byh[BATCH];   // box around the cut-off ellipse
     uint32_t id[BATCH];
 };
 
@@ -98,6 +103,24 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     s.r[k] = r2.y;
     s.g[k] = r2.z;
     s.b[k] = r2.w;
+    s.id[k] = id;
+    // |U~ d|^2 <= qcut is an ellipse with half-extents sqrt(qcut) * sqrt(diag((U~^T U~)^-1)):
+    // hy = sqrt(qcut) / u22, hx = sqrt(qcut) * sqrt(1 + (u12/u22)^2) / u11.  Inflated so
+    // that pixels the box excludes are beyond the cut-off in FP32 as well.
+    const float qc = s.qcut[k];
+    if (qc >= 0.0f) {
+        const float rq = sqrtf(qc);
+        const float ru = s.u12[k] / s.u22[k];
+        const float hy = rq / s.u22[k] * 1.001f + 1e-3f;
+        const float hx = rq * sqrtf(1.0f + ru * ru) / s.u11[k] * 1.001f + 1e-3f;
+        s.bxl[k] = r0.x - hx;
+        s.bxh[k] = r0.x + hx;
+        s.byl[k] = r0.y - hy;
+        s.byh[k] = r0.y + hy;
+    } else {
+        s.bxl[k] = s.byl[k] = 1e30f;
+        s.bxh[k] = s.byh[k] = -1e30f;
+    }
 }
 
 struct Eval {
@@ -179,14 +202,30 @@ __device__ __forceinline__ TileInfo tile_info(const RenderLaunch &p, int gtile) 
 }
 
 // ---- forward -------------------------------------------------------------------------
+// Pixel of a thread: warp w covers the 8x4 block (w % (TW/8), w / (TW/8)) of the tile.
+template <int TW>
+__device__ __forceinline__ void warp_block(const TileInfo &ti, int TH_, int &bx, int &by) {
+    const int warp = threadIdx.x >> 5;
+    bx = ti.tx * TW + (warp % (TW / 8)) * 8;
+    by = ti.ty * TH_ + (warp / (TW / 8)) * 4;
+}
+
+template <int BATCH>
+__device__ __forceinline__ bool box_hit(const Batch<BATCH> &s, int j, float xl, float xh, float yl, float yh) {
+    return s.bxh[j] >= xl && s.bxl[j] <= xh && s.byh[j] >= yl && s.byl[j] <= yh;
+}
+
 template <int TW, int TH, int BATCH, bool COUNT>
 __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s) {
     constexpr int NT = TW * TH;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const TileInfo ti = tile_info<TW, TH>(p, gtile);
-    const int px = ti.tx * TW + tid % TW, py = ti.ty * TH + tid / TW;
+    int bx, by;
+    warp_block<TW>(ti, TH, bx, by);
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < ti.W && py < ti.H;
     const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float xl = (float)bx + 0.5f, xh = (float)bx + 7.5f, yl = (float)by + 0.5f, yh = (float)by + 3.5f;
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
@@ -204,23 +243,35 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
             }
         }
         __syncthreads();
-        if (!done) {
-            const int cnt = (int)min((uint32_t)BATCH, ti.end - base);
-            for (int k = 0; k < cnt; ++k) {
-                Eval ev;
-                if (COUNT) ++c_visit;
-                const bool hit = eval_alpha<BATCH>(fpx, fpy, s, k, ev);
-                if (COUNT && ev.G >= 0.0f) ++c_full;
-                if (!hit) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
-                if (Tn < kTMin) { done = true; break; }
-                if (COUNT) ++c_comp;
-                const float w = __fmul_rn(ev.a, T);
-                C0 = __fmaf_rn(s.r[k], w, C0);
-                C1 = __fmaf_rn(s.g[k], w, C1);
-                C2 = __fmaf_rn(s.b[k], w, C2);
-                T = Tn;
-                last = base - ti.beg + k + 1;
+        const int cnt = (int)min((uint32_t)BATCH, ti.end - base);
+        bool wdone = __all_sync(0xffffffffu, done);
+        for (int c = 0; c < cnt && !wdone; c += 32) {
+            const int jl = c + lane;
+            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && box_hit<BATCH>(s, jl, xl, xh, yl, yh));
+            while (m) {
+                const int k = c + __ffs(m) - 1;
+                m &= m - 1;
+                if (!done) {
+                    Eval ev;
+                    if (COUNT) ++c_visit;
+                    const bool hit = eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+                    if (COUNT && ev.G >= 0.0f) ++c_full;
+                    if (hit) {
+                        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
+                        if (Tn < kTMin) {
+                            done = true;
+                        } else {
+                            if (COUNT) ++c_comp;
+                            const float w = __fmul_rn(ev.a, T);
+                            C0 = __fmaf_rn(s.r[k], w, C0);
+                            C1 = __fmaf_rn(s.g[k], w, C1);
+                            C2 = __fmaf_rn(s.b[k], w, C2);
+                            T = Tn;
+                            last = base - ti.beg + k + 1;
+                        }
+                    }
+                }
+                if (__all_sync(0xffffffffu, done)) { wdone = true; break; }
             }
         }
     }
@@ -238,21 +289,39 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
 }
 
 // ---- backward ------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum of v[0..11] over the warp, added to dst[0..11] by one 12-lane atomic
+// instruction.  Levels 1-4 exchange half of the live values (keep one half, send
+// the other), so lane L ends with the warp sum of component (L >> 1) & 15.
+__device__ __forceinline__ void warp_reduce_add12(float v[16], float *dst, int lane) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    return v;
+    for (int st = 0; st < 4; ++st) {
+        const int o = 16 >> st;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < (8 >> st); ++i) {
+            const int h = 8 >> st;
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const int idx = (lane >> 1) & 15;
+    if (!(lane & 1) && idx < 12) atomicAdd(dst + idx, v[0]);
 }
 
 template <int TW, int TH, int BATCH, bool COUNT>
 __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s,
-                                                BwdExtra<BATCH> &x, uint32_t &s_maxlast) {
+                                                uint32_t &s_maxlast) {
     constexpr int NT = TW * TH;
     const int tid = threadIdx.x, lane = tid & 31;
     const TileInfo ti = tile_info<TW, TH>(p, gtile);
-    const int px = ti.tx * TW + tid % TW, py = ti.ty * TH + tid / TW;
+    int bx, by;
+    warp_block<TW>(ti, TH, bx, by);
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < ti.W && py < ti.H;
     const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float xl = (float)bx + 0.5f, xh = (float)bx + 7.5f, yl = (float)by + 0.5f, yh = (float)by + 3.5f;
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
     const size_t HW = (size_t)ti.W * ti.H;
@@ -266,14 +335,15 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
         g0 = gi[pix]; g1 = gi[HW + pix]; g2 = gi[2 * HW + pix];
         T = Tf;
     }
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
     if (tid == 0) s_maxlast = 0;
     __syncthreads();
-    if (last) atomicMax(&s_maxlast, last);
+    if (lane == 0 && wlast) atomicMax(&s_maxlast, wlast);
     __syncthreads();
     const uint32_t tile_end = min(ti.end, ti.beg + s_maxlast);
     const float bgg = ti.bg[0] * g0 + ti.bg[1] * g1 + ti.bg[2] * g2;
     float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
-    float4 *grad4 = reinterpret_cast<float4 *>(p.grad2d);
+    float *grad = p.grad2d;
     unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0;
     for (uint32_t bend = tile_end; bend > ti.beg;) {
         const uint32_t bstart = (bend - ti.beg > (uint32_t)BATCH) ? bend - BATCH : ti.beg;
@@ -284,64 +354,74 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
                 stage<BATCH>(rec, id, s, k);
-                x.id[k] = id;
             }
         }
         __syncthreads();
         const int cnt = (int)(bend - bstart);
-        for (int k = cnt - 1; k >= 0; --k) {
-            const uint32_t pos = bstart + k - ti.beg;
-            Eval ev;
-            ev.G = -1.0f;
-            const bool cand = inside && pos < last;
-            bool contrib = cand && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
-            if (COUNT) { c_visit += cand; c_full += (cand && ev.G >= 0.0f); c_contrib += contrib; }
-            float gr[12];
+        const uint32_t rel0 = bstart - ti.beg;
+        for (int c = (cnt - 1) & ~31; c >= 0; c -= 32) {
+            const int jl = c + lane;
+            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && rel0 + jl < wlast &&
+                                                        box_hit<BATCH>(s, jl, xl, xh, yl, yh));
+            while (m) {
+                const int bit = 31 - __clz(m);
+                m &= ~(1u << bit);
+                const int k = c + bit;
+                const uint32_t pos = rel0 + k;
+                Eval ev;
+                ev.G = -1.0f;
+                const bool cand = inside && pos < last;
+                const bool contrib = cand && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+                if (COUNT) { c_visit += cand; c_full += (cand && ev.G >= 0.0f); c_contrib += contrib; }
+                float gr[16];
 #pragma unroll
-            for (int f = 0; f < 12; ++f) gr[f] = 0.0f;
-            if (contrib) {
-                const float one_m_a = __fsub_rn(1.0f, ev.a);
-                const float Ti = __fdividef(T, one_m_a);
-                const float w = ev.a * Ti;
-                gr[9] = w * g0; gr[10] = w * g1; gr[11] = w * g2;
-                float dLda = Ti * ((s.r[k] - S0) * g0 + (s.g[k] - S1) * g1 + (s.b[k] - S2) * g2);
-                dLda -= __fdividef(Tf * bgg, one_m_a);
-                S0 = ev.a * s.r[k] + one_m_a * S0;
-                S1 = ev.a * s.g[k] + one_m_a * S1;
-                S2 = ev.a * s.b[k] + one_m_a * S2;
-                T = Ti;
-                if (!ev.clamped) {
-                    const float dA = dLda * ev.G;
-                    gr[7] = dA * ev.P;
-                    gr[8] = dA - gr[7];
-                    const float dpow = dLda * ev.A * ev.G;
-                    const float dx = ev.dx, dy = ev.dy;
-                    gr[2] = -0.5f * dpow * dx * dx;
-                    gr[3] = -dpow * dx * dy;
-                    gr[4] = -0.5f * dpow * dy * dy;
-                    // d power / d mu-hat = conic d = U^T (U d)
-                    const float sc = dpow * kInvUScale2;
-                    gr[0] = sc * (s.u11[k] * ev.s1);
-                    gr[1] = sc * (s.u12[k] * ev.s1 + s.u22[k] * ev.s2);
-                    if (fabsf(s.wx[k]) + fabsf(s.wy[k]) < kStepDetect) {
-                        const float dz = dA * s.da[k] * ev.e * kInvSqrtPi;
-                        gr[5] = dz * dx;
-                        gr[6] = dz * dy;
-                        gr[0] -= dz * s.wx[k];
-                        gr[1] -= dz * s.wy[k];
+                for (int f = 0; f < 16; ++f) gr[f] = 0.0f;
+                if (contrib) {
+                    const float one_m_a = __fsub_rn(1.0f, ev.a);
+                    const float Ti = __fdividef(T, one_m_a);
+                    const float w = ev.a * Ti;
+                    gr[9] = w * g0; gr[10] = w * g1; gr[11] = w * g2;
+                    float dLda = Ti * ((s.r[k] - S0) * g0 + (s.g[k] - S1) * g1 + (s.b[k] - S2) * g2);
+                    dLda -= __fdividef(Tf * bgg, one_m_a);
+                    S0 = ev.a * s.r[k] + one_m_a * S0;
+                    S1 = ev.a * s.g[k] + one_m_a * S1;
+                    S2 = ev.a * s.b[k] + one_m_a * S2;
+                    T = Ti;
+                    if (!ev.clamped) {
+                        const float dA = dLda * ev.G;
+                        gr[7] = dA * ev.P;
+                        gr[8] = dA - gr[7];
+                        const float dpow = dLda * ev.A * ev.G;
+                        const float dx = ev.dx, dy = ev.dy;
+                        gr[2] = -0.5f * dpow * dx * dx;
+                        gr[3] = -dpow * dx * dy;
+                        gr[4] = -0.5f * dpow * dy * dy;
+                        // d power / d mu-hat = conic d = U^T (U d)
+                        const float sc = dpow * kInvUScale2;
+                        gr[0] = sc * (s.u11[k] * ev.s1);
+                        gr[1] = sc * (s.u12[k] * ev.s1 + s.u22[k] * ev.s2);
+                        if (fabsf(s.wx[k]) + fabsf(s.wy[k]) < kStepDetect) {
+                            const float dz = dA * s.da[k] * ev.e * kInvSqrtPi;
+                            gr[5] = dz * dx;
+                            gr[6] = dz * dy;
+                            gr[0] -= dz * s.wx[k];
+                            gr[1] -= dz * s.wy[k];
+                        }
                     }
                 }
-            }
-            const unsigned any = __ballot_sync(0xffffffffu, contrib);
-            if (COUNT && any && lane == 0) ++c_red;
-            if (any) {
-#pragma unroll
-                for (int f = 0; f < 12; ++f) gr[f] = warp_sum(gr[f]);
-                if (lane == 0) {
-                    float4 *dst = grad4 + 3 * (size_t)x.id[k];
-                    atomicAdd(dst, make_float4(gr[0], gr[1], gr[2], gr[3]));
-                    atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
-                    atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
+                const unsigned any = __ballot_sync(0xffffffffu, contrib);
+                if (!any) continue;
+                float *dst = grad + 12 * (size_t)s.id[k];
+                if (__popc(any) == 1) {
+                    if (contrib) {
+                        float4 *d4 = reinterpret_cast<float4 *>(dst);
+                        atomicAdd(d4, make_float4(gr[0], gr[1], gr[2], gr[3]));
+                        atomicAdd(d4 + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
+                        atomicAdd(d4 + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
+                    }
+                } else {
+                    if (COUNT && lane == 0) ++c_red;
+                    warp_reduce_add12(gr, dst, lane);
                 }
             }
         }
@@ -380,10 +460,9 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(RenderLaunch p) {
 template <int TW, int TH, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH) k_render_bwd(RenderLaunch p) {
     __shared__ Batch<BATCH> s;
-    __shared__ BwdExtra<BATCH> x;
     __shared__ uint32_t s_maxlast;
     if (!p.cfg.persistent) {
-        render_tile_bwd<TW, TH, BATCH, COUNT>(p, blockIdx.x, s, x, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT>(p, blockIdx.x, s, s_maxlast);
         return;
     }
     Queue *q = reinterpret_cast<Queue *>(p.ws);
@@ -394,7 +473,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(RenderLaunch p) {
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= (uint32_t)p.vt.total_tiles) break;
-        render_tile_bwd<TW, TH, BATCH, COUNT>(p, (int)order[item], s, x, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT>(p, (int)order[item], s, s_maxlast);
         __syncthreads();
     }
 }
