@@ -160,14 +160,16 @@ hgs_status hgs_project(const hgs_gaussians *g, const hgs_camera *cams_host,
 
 /* ---- A3-A5: binning ------------------------------------------------------ */
 
-/* Emits one (key, value) pair per covered tile of every (view, splat),
- * key = (global tile id << 32) | bits of depth, value = view*n + splat, in
- * (view, splat, row-major tile) order; sorts them with a stable LSD radix sort
- * (8-bit digits, onesweep with bounded decoupled look-back) over the key bits in
- * use, so that equal keys keep ascending value order; and writes per-tile
- * [start, end) ranges (ranges[2*t], ranges[2*t+1]; [0,0) for an empty tile).
- *   keys_out [pair_capacity] uint64, ids_out [pair_capacity] uint32,
- *   ranges   [2*total_tiles] uint32, dev_num_pairs: uint64, the pair count.
+/* The (tile, splat) pairs sorted by the 64-bit key (global tile id << 32) |
+ * bits of depth, one pair per covered tile of every (view, splat), ties in
+ * ascending value order (value = view*n + splat), and per-tile [start, end)
+ * ranges (ranges[2*t], ranges[2*t+1]; [0,0) for an empty tile).  This is the
+ * stable LSD radix sort (8-bit digits) of the keys over the bits in use; its
+ * four passes over the depth half run on the n_views*n per-splat depths before
+ * the splats are expanded into their tiles, which gives the same order.
+ *   keys_out [pair_capacity] uint64, optional (NULL: not written),
+ *   ids_out  [pair_capacity] uint32, ranges [2*total_tiles] uint32,
+ *   dev_num_pairs: uint64, the pair count.
  * If the count exceeds pair_capacity, HGS_DEV_CAPACITY is set, the count is
  * still written, and keys/ids/ranges are not meaningful. */
 hgs_status hgs_bin(const hgs_proj *proj, int n, const hgs_camera *cams_host, int n_views,

@@ -146,7 +146,7 @@ hgs_status hgs_bin(const hgs_proj *proj, int n, const hgs_camera *cams_host, int
     if (st != HGS_OK) return st;
     if (n < 0 || !proj_ok(proj, (long long)n * n_views) || !dev_num_pairs || !ranges) return HGS_ERR_INVALID;
     if (pair_capacity > HGS_MAX_PAIRS) return HGS_ERR_INVALID;
-    if (pair_capacity > 0 && (!keys_out || !ids_out)) return HGS_ERR_INVALID;
+    if (pair_capacity > 0 && !ids_out) return HGS_ERR_INVALID;
     if ((long long)n * n_views > 0xffffffffll) return HGS_ERR_INVALID;
     if (!ws || ws_bytes < bin_workspace_bytes(n, n_views, pair_capacity)) return HGS_ERR_CAPACITY;
     BinLaunch p;

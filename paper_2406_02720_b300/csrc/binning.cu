@@ -1,15 +1,22 @@
-// Tile binning (A3-A5): exclusive scan of tiles touched, key emission, a stable
-// LSD onesweep radix sort of the 64-bit (tile | depth) keys, and per-tile ranges.
+// Tile binning (A3-A5): the sorted (tile | depth) pairs and per-tile ranges.
 //
-// Scan: single pass with decoupled look-back over 4096-element partitions that
-// persistent blocks take in order from an atomic ticket.
-// Sort: one histogram pass over all key digits, then one onesweep pass per 8-bit
-// digit.  Each pass ranks a 4096-key partition in shared memory (warp-level
-// match_any multisplit, stable by construction), publishes per-digit counts,
-// resolves its global digit offsets by decoupled look-back over the preceding
-// partitions, and scatters through shared memory so that global writes are
-// runs of consecutive addresses.  Every spin-wait has an iteration cap; on
-// timeout it sets HGS_DEV_TIMEOUT and proceeds with the counts it has.
+// The result is the stable LSD radix sort of the 64-bit keys
+// (global tile id << 32) | bits(depth), one per covered tile of every
+// (view, splat), emitted in (view, splat) order, i.e. the order of the keys with
+// ties broken by the splat index.  It is computed in two stages:
+//   1. the four 8-bit passes over the depth half run on the n_views*n per-splat
+//      depth keys (culled splats get key 0xFFFFFFFF and sort last) -- duplicating
+//      a splat into its tiles commutes with a stable sort on depth, so these
+//      passes need not touch the much longer pair list;
+//   2. tiles touched are scanned in that depth order, each splat emits its pairs
+//      (32-bit tile key, splat index) there, and the ceil(tile_bits/8) passes over
+//      the tile half sort the pairs; the last pass writes the 64-bit keys.
+// Each radix pass is reduce-then-scan, with no inter-block waiting: an upsweep
+// counts the digits of every 4096-element partition, one warp per digit scans
+// those counts over the partitions, and a downsweep ranks each partition in
+// shared memory (warp-level match_any multisplit, stable by construction) and
+// scatters it through shared memory so that global writes are runs of
+// consecutive addresses.
 #include <algorithm>
 
 #include "hgs_internal.cuh"
@@ -22,55 +29,255 @@ constexpr int kItems = 16;                   // items per thread
 constexpr int kPart = kBlock * kItems;       // 4096 elements per partition
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;      // 256 digits
-constexpr int kMaxPasses = 8;
+constexpr int kDepthPasses = 4;              // 32 depth bits
 
-// look-back word flags (top two bits)
-constexpr uint32_t kFlagAgg32 = 1u << 30, kFlagInc32 = 2u << 30, kValMask32 = (1u << 30) - 1u;
+// look-back word flags of the pair-count scan (top two bits)
 constexpr unsigned long long kFlagAgg64 = 1ull << 62, kFlagInc64 = 2ull << 62;
 constexpr unsigned long long kValMask64 = (1ull << 62) - 1ull;
 
-struct Ctrl {                                // zeroed at the start of every hgs_bin
-    uint32_t hist[kMaxPasses][kRadix];       // global digit histograms
-    uint32_t ticket[kMaxPasses];             // partition tickets of each sort pass
+struct Ctrl {                                // zeroed at the start of every call
     uint32_t scan_ticket;
-    uint32_t pad[7];
+    uint32_t totals[kRadix];                 // per-digit totals of the current pass
+    uint32_t pad[63];
 };
 
 struct Ws {
-    uint32_t *offsets;                       // [VN] exclusive scan of tiles
-    unsigned long long *scan_state;          // [scan partitions]
     Ctrl *ctrl;
-    uint64_t *keys_alt;                      // [capacity]
-    uint32_t *ids_alt;                       // [capacity]
-    uint32_t *lookback;                      // [2][sort partitions][256]
-    size_t scan_parts, sort_parts;
+    unsigned long long *scan_state;          // [depth partitions]
+    uint32_t *dkA, *dvA, *dkB, *dvB;         // [VN] depth keys / splat indices, ping-pong
+    uint32_t *offsets;                       // [VN] pair offsets in depth order
+    uint32_t *tkA, *tvA, *tkB, *tvB;         // [capacity] tile keys / splat indices, ping-pong
+    uint32_t *counts;                        // [256][parts] digit counts, then offsets
+    size_t depth_parts, pair_parts, parts_stride;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Ws carve(void *base, size_t vn, size_t cap, size_t *total) {
     Ws w{};
-    w.scan_parts = (vn + kPart - 1) / kPart;
-    w.sort_parts = (cap + kPart - 1) / kPart;
+    w.depth_parts = std::max<size_t>((vn + kPart - 1) / kPart, 1);
+    w.pair_parts = std::max<size_t>((cap + kPart - 1) / kPart, 1);
+    w.parts_stride = std::max(w.depth_parts, w.pair_parts);
     size_t off = 0;
     char *b = static_cast<char *>(base);
     auto take = [&](size_t bytes) { char *p = b ? b + off : nullptr; off += align_up(bytes); return p; };
+    const size_t vn1 = std::max<size_t>(vn, 1), cap1 = std::max<size_t>(cap, 1);
     w.ctrl = reinterpret_cast<Ctrl *>(take(sizeof(Ctrl)));
-    w.scan_state = reinterpret_cast<unsigned long long *>(take(8 * std::max<size_t>(w.scan_parts, 1)));
-    w.offsets = reinterpret_cast<uint32_t *>(take(4 * std::max<size_t>(vn, 1)));
-    w.keys_alt = reinterpret_cast<uint64_t *>(take(8 * std::max<size_t>(cap, 1)));
-    w.ids_alt = reinterpret_cast<uint32_t *>(take(4 * std::max<size_t>(cap, 1)));
-    w.lookback = reinterpret_cast<uint32_t *>(take(4 * 2 * kRadix * std::max<size_t>(w.sort_parts, 1)));
+    w.scan_state = reinterpret_cast<unsigned long long *>(take(8 * w.depth_parts));
+    w.dkA = reinterpret_cast<uint32_t *>(take(4 * vn1));
+    w.dvA = reinterpret_cast<uint32_t *>(take(4 * vn1));
+    w.dkB = reinterpret_cast<uint32_t *>(take(4 * vn1));
+    w.dvB = reinterpret_cast<uint32_t *>(take(4 * vn1));
+    w.offsets = reinterpret_cast<uint32_t *>(take(4 * vn1));
+    w.tkA = reinterpret_cast<uint32_t *>(take(4 * cap1));
+    w.tvA = reinterpret_cast<uint32_t *>(take(4 * cap1));
+    w.tkB = reinterpret_cast<uint32_t *>(take(4 * cap1));
+    w.tvB = reinterpret_cast<uint32_t *>(take(4 * cap1));
+    w.counts = reinterpret_cast<uint32_t *>(take(4 * (size_t)kRadix * w.parts_stride));
     if (total) *total = off;
     return w;
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-// ---- A3: single-pass exclusive scan of tiles touched ---------------------------
-__global__ void __launch_bounds__(kBlock) k_scan(const uint32_t *__restrict__ in, long long n,
-                                                 uint32_t *__restrict__ out,
-                                                 unsigned long long *state, Ctrl *ctrl,
+// Element count of a pass: a host count, or a device count clamped to capacity.
+struct Count {
+    unsigned long long host;
+    const uint64_t *dev;
+    size_t capacity;
+    __device__ __forceinline__ uint32_t get() const {
+        return (uint32_t)(dev ? min((size_t)*dev, capacity) : (size_t)host);
+    }
+};
+
+// ---- stage 1: depth keys ------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_depth_keys(const uint32_t *__restrict__ tiles,
+                                                       const float *__restrict__ depth, long long vn,
+                                                       uint32_t *__restrict__ dk, uint32_t *__restrict__ dv) {
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= vn) return;
+    dk[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
+    dv[i] = (uint32_t)i;
+}
+
+// ---- radix pass, part 1: digit counts of every partition ---------------------------------
+__global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__ keys, Count cnt, int shift,
+                                                    uint32_t *__restrict__ counts, size_t stride) {
+    __shared__ uint32_t s_cnt[kBlock / 32][kRadix];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const uint32_t K = cnt.get();
+    const uint32_t n_parts = (K + kPart - 1) / kPart;
+    for (uint32_t part = blockIdx.x; part < n_parts; part += gridDim.x) {
+        for (int j = lane; j < kRadix; j += 32) s_cnt[warp][j] = 0;
+        __syncwarp();
+        const uint32_t wbase = part * kPart + warp * (32 * kItems);
+#pragma unroll 4
+        for (int it = 0; it < kItems; ++it) {
+            const uint32_t idx = wbase + it * 32 + lane;
+            const uint32_t d = idx < K ? (keys[idx] >> shift) & (kRadix - 1) : kRadix + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < (uint32_t)kRadix && lane == (uint32_t)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t total = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kBlock / 32; ++w2) total += s_cnt[w2][tid];
+        counts[(size_t)tid * stride + part] = total;
+        __syncthreads();
+    }
+}
+
+// ---- radix pass, part 2: per digit, exclusive scan of the counts over partitions ---------
+// One warp per digit; the digit totals go to ctrl->totals.
+__global__ void __launch_bounds__(kBlock) k_digit_scan(uint32_t *__restrict__ counts, Count cnt, size_t stride,
+                                                       Ctrl *ctrl) {
+    const int d = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    const int lane = lane_id();
+    if (d >= kRadix) return;
+    const uint32_t K = cnt.get();
+    const uint32_t n_parts = (K + kPart - 1) / kPart;
+    uint32_t *row = counts + (size_t)d * stride;
+    uint32_t run = 0;
+    for (uint32_t base = 0; base < n_parts; base += 32) {
+        const uint32_t j = base + lane;
+        const uint32_t v = j < n_parts ? row[j] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (j < n_parts) row[j] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) ctrl->totals[d] = run;
+}
+
+// ---- radix pass, part 3: rank and scatter ------------------------------------------------
+struct DownArgs {
+    const uint32_t *kin, *vin;
+    uint32_t *kout, *vout;
+    uint64_t *kout64;                // last pair pass, optional: (key << 32) | bits(depth[value])
+    const float *depth;
+    Count cnt;
+    int shift;
+    const uint32_t *offsets;         // [256][stride] exclusive per-digit offsets of each partition
+    size_t stride;
+    const Ctrl *ctrl;
+    int *status;
+};
+
+struct DownSmem {
+    uint32_t keys[kPart];
+    uint32_t vals[kPart];
+    uint32_t warp_cnt[kBlock / 32][kRadix];  // per-warp digit counts, then warp offsets
+    uint32_t digit_start[kRadix];            // partition-local exclusive digit prefix
+    uint32_t global_off[kRadix];             // global destination of each digit bucket
+    uint32_t digit_base[kRadix];             // exclusive prefix of the digit totals
+    uint32_t scan_tmp[kBlock / 32];
+};
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    uint32_t wb = 0;
+    for (int w2 = 0; w2 < warp; ++w2) wb += tmp[w2];
+    __syncthreads();
+    return wb + x - v;
+}
+
+template <bool COMPOSE>
+__global__ void __launch_bounds__(kBlock, 3) k_downsweep(DownArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DownSmem &sm = *reinterpret_cast<DownSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const uint32_t K = a.cnt.get();
+    const uint32_t n_parts = (K + kPart - 1) / kPart;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    sm.digit_base[tid] = block_excl_scan(a.ctrl->totals[tid], sm.scan_tmp);
+    for (uint32_t part = blockIdx.x; part < n_parts; part += gridDim.x) {
+        const uint32_t pbase = part * kPart;
+        for (int j = lane; j < kRadix; j += 32) sm.warp_cnt[warp][j] = 0;
+        sm.global_off[tid] = sm.digit_base[tid] + a.offsets[(size_t)tid * a.stride + part];
+        __syncwarp();
+        uint32_t key[kItems], val[kItems], rank[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
+            const bool valid = idx < K;
+            key[it] = valid ? a.kin[idx] : 0u;
+            val[it] = valid ? a.vin[idx] : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
+            const bool valid = idx < K;
+            const uint32_t d = valid ? (key[it] >> a.shift) & (kRadix - 1) : kRadix;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (valid && lane == leader) {
+                old = sm.warp_cnt[warp][d];
+                sm.warp_cnt[warp][d] = old + __popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[it] = old + __popc(peers & lanemask_lt);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit (thread = digit): warp offsets and partition total
+        uint32_t total = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kBlock / 32; ++w2) {
+            const uint32_t c = sm.warp_cnt[w2][tid];
+            sm.warp_cnt[w2][tid] = total;
+            total += c;
+        }
+        sm.digit_start[tid] = block_excl_scan(total, sm.scan_tmp);
+        __syncthreads();   // every digit's start is read below, not only this thread's
+        // scatter into shared memory in partition-sorted order
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
+            if (idx < K) {
+                const uint32_t d = (key[it] >> a.shift) & (kRadix - 1);
+                const uint32_t pos = sm.digit_start[d] + sm.warp_cnt[warp][d] + rank[it];
+                if (pos < (uint32_t)kPart) {
+                    sm.keys[pos] = key[it];
+                    sm.vals[pos] = val[it];
+                } else {
+                    set_status(a.status, HGS_DEV_BOUNDS);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t cnt = min((uint32_t)kPart, K - pbase);
+        for (uint32_t j = tid; j < cnt; j += kBlock) {
+            const uint32_t k = sm.keys[j];
+            const uint32_t v = sm.vals[j];
+            const uint32_t d = (k >> a.shift) & (kRadix - 1);
+            const uint32_t dst = sm.global_off[d] + (j - sm.digit_start[d]);
+            if (dst >= K) { set_status(a.status, HGS_DEV_BOUNDS); continue; }
+            a.kout[dst] = k;
+            a.vout[dst] = v;
+            if (COMPOSE) a.kout64[dst] = ((uint64_t)k << 32) | (uint64_t)__float_as_uint(a.depth[v]);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- stage 2: exclusive scan of tiles touched, in depth order -----------------------------
+__global__ void __launch_bounds__(kBlock) k_scan(const uint32_t *__restrict__ tiles,
+                                                 const uint32_t *__restrict__ order, long long n,
+                                                 uint32_t *__restrict__ out, unsigned long long *state, Ctrl *ctrl,
                                                  uint64_t *total_out, int *status) {
     __shared__ unsigned long long s_warp[kBlock / 32];
     __shared__ unsigned long long s_prefix;
@@ -85,24 +292,23 @@ __global__ void __launch_bounds__(kBlock) k_scan(const uint32_t *__restrict__ in
         const long long base = part * kPart + (long long)threadIdx.x * kItems;
         uint32_t v[kItems];
         if (base + kItems <= n) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(in + base);
+            const uint4 *src = reinterpret_cast<const uint4 *>(order + base);
 #pragma unroll
             for (int j = 0; j < kItems / 4; ++j) {
-                uint4 t = src[j];
-                v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+                const uint4 t = src[j];
+                v[4 * j] = tiles[t.x]; v[4 * j + 1] = tiles[t.y]; v[4 * j + 2] = tiles[t.z]; v[4 * j + 3] = tiles[t.w];
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < kItems; ++j) v[j] = (base + j < n) ? in[base + j] : 0u;
+            for (int j = 0; j < kItems; ++j) v[j] = (base + j < n) ? tiles[order[base + j]] : 0u;
         }
         unsigned long long tsum = 0;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) tsum += v[j];
-        // block exclusive scan of the thread sums
         unsigned long long x = tsum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
             if (lane >= d) x += y;
         }
         if (lane == 31) s_warp[warp] = x;
@@ -113,26 +319,25 @@ __global__ void __launch_bounds__(kBlock) k_scan(const uint32_t *__restrict__ in
             if (w2 < warp) wbase += s_warp[w2];
             agg += s_warp[w2];
         }
-        unsigned long long texcl = wbase + x - tsum;
-        // decoupled look-back by warp 0
+        const unsigned long long texcl = wbase + x - tsum;
+        // decoupled look-back by warp 0, 32 predecessors at a time
         if (warp == 0) {
-            if (lane == 0)
-                st_relaxed_u64(&state[part], (part == 0 ? kFlagInc64 : kFlagAgg64) | agg);
+            if (lane == 0) st_relaxed_u64(&state[part], (part == 0 ? kFlagInc64 : kFlagAgg64) | agg);
             unsigned long long excl = 0;
             long long j = part - 1;
             unsigned spins = 0;
             bool timed_out = false;
             while (j >= 0) {
-                long long idx = j - lane;
+                const long long idx = j - lane;
                 unsigned long long w = idx >= 0 ? ld_relaxed_u64(&state[idx]) : kFlagInc64;
                 while (__any_sync(0xffffffffu, (w >> 62) == 0)) {
                     if (++spins > kSpinCap) { timed_out = true; break; }
                     __nanosleep(kSpinSleepNs);
                     if ((w >> 62) == 0) w = ld_relaxed_u64(&state[idx]);
                 }
-                if (timed_out) { if ((w >> 62) == 0) w = kFlagInc64; }
-                unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2);
-                int stop = inc ? __ffs(inc) - 1 : 31;
+                if (timed_out && (w >> 62) == 0) w = kFlagInc64;
+                const unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+                const int stop = inc ? __ffs(inc) - 1 : 31;
                 unsigned long long val = (lane <= stop) ? (w & kValMask64) : 0ull;
 #pragma unroll
                 for (int d = 16; d > 0; d >>= 1) val += __shfl_xor_sync(0xffffffffu, val, d);
@@ -158,234 +363,124 @@ __global__ void __launch_bounds__(kBlock) k_scan(const uint32_t *__restrict__ in
     }
 }
 
-// ---- A3: key emission ---------------------------------------------------------------
+// ---- stage 2: pair emission in depth order ---------------------------------------------------
+// A warp expands its 32 splats' pairs cooperatively: pair q of the warp (in
+// order) belongs to the last lane whose start is <= q, so consecutive lanes
+// write consecutive addresses however uneven the splats' tile counts are.
 struct DupArgs {
     const uint32_t *tiles;
     const int4 *rect;
-    const float *depth;
-    const uint32_t *offsets;
-    const uint64_t *num_pairs;
+    const uint32_t *order;      // splat indices in depth order
+    const uint32_t *offsets;    // pair offsets in depth order
     long long vn;
     int n;
     ViewTable vt;
     size_t capacity;
-    uint64_t *keys;
-    uint32_t *ids;
+    uint32_t *tk, *tv;
     int *status;
 };
 
 __global__ void __launch_bounds__(kBlock) k_duplicate(DupArgs a) {
-    const long long vi = (long long)blockIdx.x * kBlock + threadIdx.x;
-    if (vi >= a.vn) return;
-    const uint32_t cnt = a.tiles[vi];
-    if (cnt == 0) return;
-    const uint64_t off = a.offsets[vi];
-    if (off + cnt > a.capacity) set_status(a.status, HGS_DEV_CAPACITY);
-    const int v = (int)(vi / a.n);
-    const int4 r = a.rect[vi];
-    const uint64_t db = __float_as_uint(a.depth[vi]);
-    const int tx = a.vt.tiles_x[v];
-    const int gbase = a.vt.tile_off[v];
-    uint64_t j = off;
-    for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx2 = r.x; tx2 < r.z; ++tx2, ++j) {
-            if (j >= a.capacity) return;
-            a.keys[j] = ((uint64_t)(gbase + ty * tx + tx2) << 32) | db;
-            a.ids[j] = (uint32_t)vi;
-        }
-}
-
-// ---- A4: digit histograms for all passes (and look-back region 0 cleared) ------------
-__global__ void __launch_bounds__(kBlock) k_hist(const uint64_t *__restrict__ keys,
-                                                 const uint64_t *num_pairs, size_t capacity,
-                                                 int npass, Ctrl *ctrl, uint32_t *lookback0) {
-    __shared__ uint32_t s_hist[kMaxPasses][kRadix];
-    for (int j = threadIdx.x; j < kMaxPasses * kRadix; j += kBlock) (&s_hist[0][0])[j] = 0;
-    __syncthreads();
-    const size_t K = min((size_t)*num_pairs, capacity);
-    const size_t parts = (K + kPart - 1) / kPart;
-    const size_t stride = (size_t)gridDim.x * kBlock;
-    for (size_t j = (size_t)blockIdx.x * kBlock + threadIdx.x; j < parts * kRadix; j += stride) lookback0[j] = 0;
-    const size_t rounds = (K + stride - 1) / stride;
-    for (size_t r = 0; r < rounds; ++r) {
-        const size_t j = r * stride + (size_t)blockIdx.x * kBlock + threadIdx.x;
-        const bool valid = j < K;
-        const uint64_t key = valid ? keys[j] : 0ull;
-        for (int p = 0; p < npass; ++p) {
-            const uint32_t d = valid ? (uint32_t)(key >> (kRadixBits * p)) & (kRadix - 1) : kRadix + lane_id();
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[p][d], __popc(peers));
-        }
+    __shared__ uint32_t s_start[kBlock / 32][32];
+    __shared__ int s_x0[kBlock / 32][32], s_w[kBlock / 32][32], s_row0[kBlock / 32][32], s_txn[kBlock / 32][32];
+    __shared__ uint32_t s_vi[kBlock / 32][32];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const long long j0 = (long long)blockIdx.x * kBlock + warp * 32;
+    if (j0 >= a.vn) return;
+    const long long j = j0 + lane;
+    uint32_t vi = 0, cnt = 0;
+    int4 r = make_int4(0, 0, 0, 0);
+    if (j < a.vn) {
+        vi = a.order[j];
+        cnt = a.tiles[vi];
+        if (cnt) r = a.rect[vi];
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < npass * kRadix; j += kBlock) {
-        uint32_t c = (&s_hist[0][0])[j];
-        if (c) atomicAdd(&(&ctrl->hist[0][0])[j], c);
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    if (total == 0) return;
+    const uint64_t wbase = a.offsets[j0];
+    const int v = (int)(vi / (uint32_t)a.n);
+    s_start[warp][lane] = x - cnt;
+    s_x0[warp][lane] = r.x;
+    s_w[warp][lane] = r.z - r.x;
+    s_txn[warp][lane] = a.vt.tiles_x[v];
+    s_row0[warp][lane] = a.vt.tile_off[v] + r.y * a.vt.tiles_x[v];
+    s_vi[warp][lane] = vi;
+    __syncwarp();
+    if (wbase + total > a.capacity && lane == 0) set_status(a.status, HGS_DEV_CAPACITY);
+    for (uint32_t q = lane; q < total; q += 32) {
+        int s = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (s + step < 32 && s_start[warp][s + step] <= q) s += step;
+        const uint32_t local = q - s_start[warp][s];
+        const uint32_t w = (uint32_t)s_w[warp][s];
+        const uint32_t ty = local / w, tx = local - ty * w;
+        const uint64_t dst = wbase + q;
+        if (dst >= a.capacity) break;
+        a.tk[dst] = (uint32_t)(s_row0[warp][s] + (int)ty * s_txn[warp][s] + s_x0[warp][s] + (int)tx);
+        a.tv[dst] = s_vi[warp][s];
     }
 }
 
-// ---- A4: one onesweep pass -------------------------------------------------------------
-struct SweepSmem {
-    uint64_t keys[kPart];
-    uint32_t vals[kPart];
-    uint32_t warp_cnt[kBlock / 32][kRadix];  // per-warp digit counts, then warp offsets
-    uint32_t digit_start[kRadix];            // partition-local exclusive digit prefix
-    uint32_t global_off[kRadix];             // global destination of each digit bucket
-    uint32_t digit_base[kRadix];             // exclusive prefix of the global histogram
-    uint32_t part;
-    uint32_t scan_tmp[kBlock / 32];
-};
-
-__global__ void __launch_bounds__(kBlock) k_onesweep(int pass, const uint64_t *__restrict__ kin,
-                                                     const uint32_t *__restrict__ vin,
-                                                     uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                     const uint64_t *num_pairs, size_t capacity,
-                                                     Ctrl *ctrl, uint32_t *lookback, uint32_t *lookback_next,
-                                                     int *status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SweepSmem &sm = *reinterpret_cast<SweepSmem *>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
-    const uint32_t K = (uint32_t)min((size_t)*num_pairs, capacity);
-    const uint32_t n_parts = (K + kPart - 1) / kPart;
-    const int shift = kRadixBits * pass;
-    const unsigned lanemask_lt = (1u << lane) - 1u;
-
-    // exclusive prefix of the global histogram of this digit (thread = digit)
-    {
-        uint32_t c = ctrl->hist[pass][tid];
-        uint32_t x = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
-        }
-        if (lane == 31) sm.scan_tmp[warp] = x;
-        __syncthreads();
-        uint32_t wb = 0;
-        for (int w2 = 0; w2 < warp; ++w2) wb += sm.scan_tmp[w2];
-        sm.digit_base[tid] = wb + x - c;
-        __syncthreads();
-    }
-
-    for (;;) {
-        if (tid == 0) sm.part = atomicAdd(&ctrl->ticket[pass], 1u);
-        __syncthreads();
-        const uint32_t part = sm.part;
-        if (part >= n_parts) break;
-        // clear this partition's word row in the next pass's look-back region
-        if (lookback_next) lookback_next[(size_t)part * kRadix + tid] = 0;
-        const uint32_t pbase = part * kPart;
-        for (int j = lane; j < kRadix; j += 32) sm.warp_cnt[warp][j] = 0;
-        __syncwarp();
-        uint64_t key[kItems];
-        uint32_t val[kItems];
-        uint32_t rank[kItems];
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
-            const bool valid = idx < K;
-            key[it] = valid ? kin[idx] : 0ull;
-            val[it] = valid ? vin[idx] : 0u;
-            const uint32_t d = valid ? (uint32_t)(key[it] >> shift) & (kRadix - 1) : kRadix;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (valid && lane == leader) {
-                old = sm.warp_cnt[warp][d];
-                sm.warp_cnt[warp][d] = old + __popc(peers);
-            }
-            old = __shfl_sync(0xffffffffu, old, leader);
-            rank[it] = old + __popc(peers & lanemask_lt);
-            __syncwarp();
-        }
-        __syncthreads();
-        // per digit (thread = digit): warp offsets and partition total
-        uint32_t total = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < kBlock / 32; ++w2) {
-            uint32_t c = sm.warp_cnt[w2][tid];
-            sm.warp_cnt[w2][tid] = total;
-            total += c;
-        }
-        uint32_t *row = lookback + (size_t)part * kRadix;
-        st_relaxed_u32(&row[tid], (part == 0 ? kFlagInc32 : kFlagAgg32) | total);
-        // partition-local exclusive prefix over digits
-        {
-            uint32_t x = total;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-                if (lane >= d) x += y;
-            }
-            if (lane == 31) sm.scan_tmp[warp] = x;
-            __syncthreads();
-            uint32_t wb = 0;
-            for (int w2 = 0; w2 < warp; ++w2) wb += sm.scan_tmp[w2];
-            sm.digit_start[tid] = wb + x - total;
-        }
-        // decoupled look-back for this digit
-        uint32_t excl = 0;
-        if (part > 0) {
-            int j = (int)part - 1;
-            unsigned spins = 0;
-            while (j >= 0) {
-                uint32_t w = ld_relaxed_u32(&lookback[(size_t)j * kRadix + tid]);
-                uint32_t flag = w & ~kValMask32;
-                if (flag == 0) {
-                    if (++spins > kSpinCap) { set_status(status, HGS_DEV_TIMEOUT); break; }
-                    __nanosleep(kSpinSleepNs);
-                    continue;
-                }
-                excl += w & kValMask32;
-                if (flag == kFlagInc32) break;
-                --j;
-            }
-            st_relaxed_u32(&row[tid], kFlagInc32 | ((excl + total) & kValMask32));
-        }
-        sm.global_off[tid] = sm.digit_base[tid] + excl;
-        __syncthreads();
-        // scatter into shared memory in partition-sorted order
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
-            if (idx < K) {
-                const uint32_t d = (uint32_t)(key[it] >> shift) & (kRadix - 1);
-                const uint32_t pos = sm.digit_start[d] + sm.warp_cnt[warp][d] + rank[it];
-                sm.keys[pos] = key[it];
-                sm.vals[pos] = val[it];
-            }
-        }
-        __syncthreads();
-        const uint32_t cnt = min((uint32_t)kPart, K - pbase);
-        for (uint32_t j = tid; j < cnt; j += kBlock) {
-            const uint64_t k = sm.keys[j];
-            const uint32_t d = (uint32_t)(k >> shift) & (kRadix - 1);
-            const uint32_t dst = sm.global_off[d] + (j - sm.digit_start[d]);
-            if (dst < capacity) {
-                kout[dst] = k;
-                vout[dst] = sm.vals[j];
-            } else {
-                set_status(status, HGS_DEV_BOUNDS);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ---- A5: tile ranges -----------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_ranges(const uint64_t *__restrict__ keys,
-                                                   const uint64_t *num_pairs, size_t capacity,
-                                                   int total_tiles, uint32_t *ranges, int *status) {
-    const size_t K = min((size_t)*num_pairs, capacity);
+// ---- A5: tile ranges from the sorted 32-bit tile keys ------------------------------------
+__global__ void __launch_bounds__(kBlock) k_ranges(const uint32_t *__restrict__ tk, Count cnt, int total_tiles,
+                                                   uint32_t *ranges, int *status) {
+    const size_t K = cnt.get();
     for (size_t i = (size_t)blockIdx.x * kBlock + threadIdx.x; i < K; i += (size_t)gridDim.x * kBlock) {
-        const uint32_t t = (uint32_t)(keys[i] >> 32);
+        const uint32_t t = tk[i];
         if (t >= (uint32_t)total_tiles) { set_status(status, HGS_DEV_BOUNDS); continue; }
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)i;
-        if (i == K - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
+        if (i == 0 || tk[i - 1] != t) ranges[2 * (size_t)t] = (uint32_t)i;
+        if (i == K - 1 || tk[i + 1] != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
     }
 }
 
 int g_sweep_blocks = 0, g_aux_blocks = 0;
+
+void init_launch_shapes() {
+    if (g_sweep_blocks) return;
+    const int sms = num_sms();
+    int occ = 0, occ2 = 0;
+    cudaFuncSetAttribute(k_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
+    cudaFuncSetAttribute(k_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_downsweep<false>, kBlock, sizeof(DownSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_upsweep, kBlock, 0);
+    g_sweep_blocks = sms * std::max(occ, 1);
+    g_aux_blocks = sms * std::max(occ2, 1);
+}
+
+// One radix pass over cnt elements: upsweep, digit scan, downsweep.
+cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout, uint64_t *kout64,
+                       const float *depth, Count cnt, size_t max_elems, int shift, const Ws &w, int *status,
+                       cudaStream_t s) {
+    const int parts = (int)std::max<size_t>((max_elems + kPart - 1) / kPart, 1);
+    k_upsweep<<<std::min(parts, g_aux_blocks), kBlock, 0, s>>>(kin, cnt, shift, w.counts, w.parts_stride);
+    k_digit_scan<<<kRadix / (kBlock / 32), kBlock, 0, s>>>(w.counts, cnt, w.parts_stride, w.ctrl);
+    DownArgs a{};
+    a.kin = kin;
+    a.vin = vin;
+    a.kout = kout;
+    a.vout = vout;
+    a.kout64 = kout64;
+    a.depth = depth;
+    a.cnt = cnt;
+    a.shift = shift;
+    a.offsets = w.counts;
+    a.stride = w.parts_stride;
+    a.ctrl = w.ctrl;
+    a.status = status;
+    const int grid = std::min(parts, g_sweep_blocks);
+    if (kout64)
+        k_downsweep<true><<<grid, kBlock, sizeof(DownSmem), s>>>(a);
+    else
+        k_downsweep<false><<<grid, kBlock, sizeof(DownSmem), s>>>(a);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -402,68 +497,58 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
     if (need > p.ws_bytes) return cudaErrorInvalidValue;
     cudaError_t e;
     const int total_tiles = p.vt.total_tiles;
-    // key bits in use: 32 depth bits + enough for the largest global tile id
     int tile_bits = 1;
     while ((1ll << tile_bits) < (long long)total_tiles) ++tile_bits;
-    const int key_bits = 32 + tile_bits;
-    const int npass = (key_bits + kRadixBits - 1) / kRadixBits;
-    // where the unsorted pairs go so that the last pass lands in keys_out/ids_out
-    uint64_t *kA = (npass % 2 == 0) ? p.keys_out : w.keys_alt;
-    uint32_t *iA = (npass % 2 == 0) ? p.ids_out : w.ids_alt;
-    uint64_t *kB = (npass % 2 == 0) ? w.keys_alt : p.keys_out;
-    uint32_t *iB = (npass % 2 == 0) ? w.ids_alt : p.ids_out;
-
-    if (g_sweep_blocks == 0) {
-        const int sms = num_sms();
-        int occ = 0;
-        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SweepSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_onesweep, kBlock, sizeof(SweepSmem));
-        g_sweep_blocks = sms * std::max(occ, 1);
-        int occ2 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_scan, kBlock, 0);
-        g_aux_blocks = sms * std::max(occ2, 1);
-    }
+    const int tile_passes = (tile_bits + kRadixBits - 1) / kRadixBits;
+    init_launch_shapes();
     if ((e = cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.scan_state, 0, 8 * std::max<size_t>(w.scan_parts, 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.scan_state, 0, 8 * w.depth_parts, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.num_pairs, 0, sizeof(uint64_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, s)) != cudaSuccess) return e;
     if (vn == 0) return cudaSuccess;
-    {
-        int grid = (int)std::min<size_t>(w.scan_parts, (size_t)g_aux_blocks);
-        k_scan<<<grid, kBlock, 0, s>>>(p.proj->tiles, (long long)vn, w.offsets, w.scan_state, w.ctrl,
-                                       p.num_pairs, p.status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    {
-        DupArgs d;
-        d.tiles = p.proj->tiles;
-        d.rect = reinterpret_cast<const int4 *>(p.proj->rect);
-        d.depth = p.proj->depth;
-        d.offsets = w.offsets;
-        d.num_pairs = p.num_pairs;
-        d.vn = (long long)vn;
-        d.n = p.n;
-        d.vt = p.vt;
-        d.capacity = p.capacity;
-        d.keys = kA;
-        d.ids = iA;
-        d.status = p.status;
-        k_duplicate<<<(unsigned)((vn + kBlock - 1) / kBlock), kBlock, 0, s>>>(d);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    k_hist<<<g_aux_blocks, kBlock, 0, s>>>(kA, p.num_pairs, p.capacity, npass, w.ctrl, w.lookback);
+
+    // stage 1: depth keys, four passes over them (the order ends in dkA/dvA)
+    k_depth_keys<<<(unsigned)((vn + kBlock - 1) / kBlock), kBlock, 0, s>>>(p.proj->tiles, p.proj->depth,
+                                                                           (long long)vn, w.dkA, w.dvA);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t region = (size_t)kRadix * std::max<size_t>(w.sort_parts, 1);
-    for (int pass = 0; pass < npass; ++pass) {
+    const Count cnt_vn{vn, nullptr, vn};
+    for (int pass = 0; pass < kDepthPasses; ++pass) {
         const bool even = (pass % 2) == 0;
-        uint32_t *lb = w.lookback + (even ? 0 : region);
-        uint32_t *lb_next = (pass + 1 < npass) ? w.lookback + (even ? region : 0) : nullptr;
-        k_onesweep<<<g_sweep_blocks, kBlock, sizeof(SweepSmem), s>>>(
-            pass, even ? kA : kB, even ? iA : iB, even ? kB : kA, even ? iB : iA, p.num_pairs, p.capacity,
-            w.ctrl, lb, lb_next, p.status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = radix_pass(even ? w.dkA : w.dkB, even ? w.dvA : w.dvB, even ? w.dkB : w.dkA, even ? w.dvB : w.dvA,
+                       nullptr, nullptr, cnt_vn, vn, kRadixBits * pass, w, p.status, s);
+        if (e != cudaSuccess) return e;
     }
-    k_ranges<<<g_aux_blocks, kBlock, 0, s>>>(p.keys_out, p.num_pairs, p.capacity, total_tiles, p.ranges, p.status);
+
+    // stage 2: pair offsets in depth order, pair emission, passes over the tile half
+    k_scan<<<std::min<size_t>(w.depth_parts, (size_t)g_aux_blocks), kBlock, 0, s>>>(
+        p.proj->tiles, w.dvA, (long long)vn, w.offsets, w.scan_state, w.ctrl, p.num_pairs, p.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    DupArgs d;
+    d.tiles = p.proj->tiles;
+    d.rect = reinterpret_cast<const int4 *>(p.proj->rect);
+    d.order = w.dvA;
+    d.offsets = w.offsets;
+    d.vn = (long long)vn;
+    d.n = p.n;
+    d.vt = p.vt;
+    d.capacity = p.capacity;
+    d.tk = w.tkA;
+    d.tv = w.tvA;
+    d.status = p.status;
+    k_duplicate<<<(unsigned)((vn + kBlock - 1) / kBlock), kBlock, 0, s>>>(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const Count cnt_k{0, p.num_pairs, p.capacity};
+    for (int pass = 0; pass < tile_passes; ++pass) {
+        const bool even = (pass % 2) == 0;
+        const bool last = pass + 1 == tile_passes;
+        uint32_t *kout = even ? w.tkB : w.tkA;
+        uint32_t *vout = last ? p.ids_out : (even ? w.tvB : w.tvA);
+        e = radix_pass(even ? w.tkA : w.tkB, even ? w.tvA : w.tvB, kout, vout, last ? p.keys_out : nullptr,
+                       p.proj->depth, cnt_k, p.capacity, kRadixBits * pass, w, p.status, s);
+        if (e != cudaSuccess) return e;
+    }
+    const uint32_t *tiles_sorted = (tile_passes % 2) ? w.tkB : w.tkA;
+    k_ranges<<<g_aux_blocks, kBlock, 0, s>>>(tiles_sorted, cnt_k, total_tiles, p.ranges, p.status);
     return cudaGetLastError();
 }
 

@@ -71,8 +71,9 @@ class Rasterizer:
     Pair capacity grows automatically when a step reports HGS_DEV_CAPACITY (the
     step is then re-run outside any graph)."""
 
-    def __init__(self, cams, n, config=None, pair_capacity=None, device="cuda"):
+    def __init__(self, cams, n, config=None, pair_capacity=None, device="cuda", keep_keys=False):
         self.device = torch.device(device)
+        self.keep_keys = keep_keys          # also write the sorted 64-bit keys (not needed to render)
         self.cfg = config if config is not None else H.make_config()
         self.cams_list = list(cams)
         self.n_views = len(self.cams_list)
@@ -105,7 +106,7 @@ class Rasterizer:
         if cap == self.capacity:
             return
         self.capacity = cap
-        self.keys = torch.empty(cap, dtype=torch.int64, device=self.device)
+        self.keys = torch.empty(cap if self.keep_keys else 0, dtype=torch.int64, device=self.device)
         self.ids = torch.empty(cap, dtype=torch.int32, device=self.device)
         wsb = H.hgs_bin_workspace_size(self.n, self.n_views, cap)
         self.bin_ws = torch.empty(wsb, dtype=torch.uint8, device=self.device)
@@ -219,7 +220,7 @@ class Rasterizer:
 
     def sorted_pairs(self):
         k = int(self.num_pairs.item())
-        return self.keys[:k], self.ids[:k]
+        return (self.keys[:k] if self.keep_keys else None), self.ids[:k]
 
 
 class HGSRasterize(torch.autograd.Function):

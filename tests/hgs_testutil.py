@@ -29,7 +29,7 @@ def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persi
     from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
     cfg = H.make_config(tile=tile, batch=batch, lowpass=lowpass, plain=plain, persistent=persistent)
     g = Gaussians.from_scene(sc)
-    r = Rasterizer(cams, sc.n, cfg, pair_capacity=pair_capacity)
+    r = Rasterizer(cams, sc.n, cfg, pair_capacity=pair_capacity, keep_keys=True)
     r.forward(g)
     out = dict(rast=r, g=g)
     out["images"] = [x.cpu().numpy() for x in r.images()]

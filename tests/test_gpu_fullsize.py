@@ -33,7 +33,7 @@ def test_config3_sampled_parity(cuda_ok):
     W, Hh = cam.width, cam.height
     cfg = H.make_config(tile=(16, 16), batch=0)
     g = Gaussians.from_scene(sc)
-    r = Rasterizer(cams, sc.n, cfg)
+    r = Rasterizer(cams, sc.n, cfg, keep_keys=True)
     r.forward(g)
     ranges = r.ranges.cpu().numpy().view(np.uint32)
     keys = r.keys[:int(r.num_pairs.item())].cpu().numpy().view(np.uint64)

@@ -173,7 +173,7 @@ def test_capacity_overflow_sets_status_and_count(cuda_ok):
     from paper_2406_02720_b300 import hgs as H
     from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
     sc, cams = scenes.config1()
-    r = Rasterizer(cams, sc.n, H.make_config(), pair_capacity=100)
+    r = Rasterizer(cams, sc.n, H.make_config(), pair_capacity=100, keep_keys=True)
     g = Gaussians.from_scene(sc)
     r.clear_status()
     r.project(g)

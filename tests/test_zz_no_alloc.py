@@ -48,7 +48,7 @@ def test_static_scratch_binning_matches_caller_scratch(cuda_ok):
     from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
     for seed, n in ((21, 1500), (22, 900)):          # two calls in a row, different sizes
         sc, cams = _scene(seed, n)
-        r = Rasterizer(cams, sc.n, H.make_config())
+        r = Rasterizer(cams, sc.n, H.make_config(), keep_keys=True)
         r.forward(Gaussians.from_scene(sc))          # projection + hgs_bin with caller scratch
         k_ref, i_ref = (x.cpu().numpy() for x in r.sorted_pairs())
         rng_ref = r.ranges.cpu().numpy()
