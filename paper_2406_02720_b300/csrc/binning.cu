@@ -14,7 +14,8 @@
 // Each radix pass is reduce-then-scan, with no inter-block waiting: an upsweep
 // counts the digits of every 4096-element partition, one warp per digit scans
 // those counts over the partitions, and a downsweep ranks each partition in
-// shared memory (warp-level match_any multisplit, stable by construction) and
+// shared memory (warp-level multisplit from per-bit ballots, stable by
+// construction) and
 // scatters it through shared memory so that global writes are runs of
 // consecutive addresses.
 #include <algorithm>
@@ -80,6 +81,20 @@ Ws carve(void *base, size_t vn, size_t cap, size_t *total) {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
+// Lanes of the warp holding the same 9-bit value v (digits 0..255, 256 for an
+// empty slot): the AND over the bits of v of the ballot of that bit or of its
+// complement.  Nine ballots, whatever the number of distinct values.
+__device__ __forceinline__ unsigned peer_mask(uint32_t v) {
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const bool bit = (v >> b) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
 // Element count of a pass: a host count, or a device count clamped to capacity.
 struct Count {
     unsigned long long host;
@@ -114,10 +129,7 @@ __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__
 #pragma unroll 4
         for (int it = 0; it < kItems; ++it) {
             const uint32_t idx = wbase + it * 32 + lane;
-            const uint32_t d = idx < K ? (keys[idx] >> shift) & (kRadix - 1) : kRadix + lane;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (d < (uint32_t)kRadix && lane == (uint32_t)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
-            __syncwarp();
+            if (idx < K) atomicAdd(&s_cnt[warp][(keys[idx] >> shift) & (kRadix - 1)], 1u);
         }
         __syncthreads();
         uint32_t total = 0;
@@ -221,7 +233,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_downsweep(DownArgs a) {
             const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
             const bool valid = idx < K;
             const uint32_t d = valid ? (key[it] >> a.shift) & (kRadix - 1) : kRadix;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const unsigned peers = peer_mask(d);
             const int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (valid && lane == leader) {
