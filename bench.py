@@ -239,6 +239,10 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e, "gpu_launches": launches * args.steps,
     }
+    if args.multiview:
+        del step, fwd_step
+        torch.cuda.empty_cache()
+        result["multiview"] = run_multiview(args, dev)
     if rank == 0 and args.cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
     if dist_mod:
@@ -362,6 +366,45 @@ def run_e2e(args, rast, g, dL, grads, step, pixels, dev):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+# ---- batched multi-view vs one launch sequence per view ----------------------------------------
+def run_multiview(args, dev):
+    """64 cameras of uneven size over a 1M-splat scene: views/s of the batched
+    persistent path against the per-view path, both CUDA-graph captured, same
+    tile shape (autotuned for the batched path) and the same images."""
+    import torch
+    from paper_2406_02720_b300 import autotune, scenes
+    from paper_2406_02720_b300.multiview import BatchedStep, PerViewStep, packed_upstream, time_replays
+    from paper_2406_02720_b300.rasterizer import Gaussians
+    sc, cams = scenes.config4(n=args.mv_n, n_views=args.mv_views)
+    dL = scenes.upstream_grad(104, cams)
+    g = Gaussians.from_scene(sc, dev)
+    dLp = packed_upstream(dL, dev)
+    cache = os.path.join(os.path.expanduser("~"), ".cache", "hgs_b300", "autotune.json")
+    tile, batch, timings = autotune.tune(cams, g, dLp, steps=3, cache_path=cache, device=dev)
+    b = BatchedStep(cams, g, dLp, tile=tile, batch=batch, device=dev)
+    ms_b = time_replays(b, args.mv_steps)
+    st_b = b.status()
+    imgs_b = [x.clone() for x in b.images()]
+    pairs = int(b.rast.num_pairs.item())
+    del b
+    torch.cuda.empty_cache()
+    p = PerViewStep(cams, g, dL, tile=tile, batch=batch, device=dev)
+    ms_p = time_replays(p, args.mv_steps)
+    st_p = p.status()
+    same = all(bool(torch.equal(x, y)) for x, y in zip(imgs_b, p.images()))
+    del p
+    torch.cuda.empty_cache()
+    V = len(cams)
+    pix = sum(c.width * c.height for c in cams)
+    return {"workload": f"config4: {sc.n} half-Gaussians, {V} cameras on a sphere, sizes from "
+                        "{640x360, 1280x720, 1600x900, 1920x1080}, fwd+bwd, CUDA graph",
+            "views": V, "pixels_per_step": pix, "pairs": pairs, "tile": list(tile), "batch": batch,
+            "autotune_ms": timings, "batched_ms_per_step": ms_b, "per_view_ms_per_step": ms_p,
+            "batched_views_per_s": V / (ms_b * 1e-3), "per_view_views_per_s": V / (ms_p * 1e-3),
+            "speedup": ms_p / ms_b, "batched_Mpixel_per_s": pix / (ms_b * 1e3),
+            "images_identical": same, "status": st_b | st_p, "steps": args.mv_steps}
+
+
 # ---- CPU oracle (reported baseline / reference arm) -----------------------------------------
 def cpu_baseline(args, n_tiles_sample=48, seed=5):
     """FP64 oracle on a bounded sample: full projection and projection adjoint of all
@@ -432,6 +475,10 @@ def main(argv=None):
     ap.add_argument("--tile-h", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-multiview", dest="multiview", action="store_false")
+    ap.add_argument("--mv-views", type=int, default=64)
+    ap.add_argument("--mv-n", type=int, default=1_000_000)
+    ap.add_argument("--mv-steps", type=int, default=10)
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -78,7 +78,8 @@ typedef struct {
     int sh_degree;
 } hgs_gaussians;
 
-/* Gradients, same shapes as hgs_gaussians (written, not accumulated). */
+/* Gradients, same shapes as hgs_gaussians (written, or added into when
+ * hgs_config.accumulate is set). */
 typedef struct {
     float *means, *scales, *quats, *normals, *opac1, *opac2, *sh;
 } hgs_gaussian_grads;
@@ -104,7 +105,10 @@ typedef struct {
  *   fov_clamp      : 1 = clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS)
  *   plain          : 1 = plain 3D-GS weight alpha1 * hat G (no half split)
  *   persistent     : 1 = one persistent launch over a (view, tile) work queue,
- *                    0 = one thread block per tile                            */
+ *                    0 = one thread block per tile
+ *   accumulate     : 1 = hgs_project_bwd / hgs_render_bwd add into the
+ *                    gradient buffers instead of overwriting them (to sum
+ *                    gradients over several calls, e.g. one call per view)   */
 typedef struct {
     int tile_w, tile_h;
     int batch;
@@ -112,6 +116,7 @@ typedef struct {
     int fov_clamp;
     int plain;
     int persistent;
+    int accumulate;
 } hgs_config;
 
 /* Per-(view, splat) projected records written by hgs_project, [n_views*n] rows.
@@ -234,7 +239,8 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids,
 /* ---- A8: projection backward ------------------------------------------------ */
 
 /* Chain rule from grad2d through Eq. 8, Eq. 3-5, Eq. 2 and the SH colour to
- * every parameter, summed over views.  Writes every entry of `out`. */
+ * every parameter, summed over views.  Writes every entry of `out` (adds into
+ * it when cfg->accumulate is set). */
 hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host,
                            const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                            const float *grad2d, const hgs_gaussian_grads *out,

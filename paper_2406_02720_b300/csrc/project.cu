@@ -731,22 +731,30 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) 
 #pragma unroll
             for (int k = 0; k < 3; ++k) gm[k] += (gd[k] - dd * dir[k]) * il;
         }
+        const bool acc = p.cfg.accumulate != 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            p.out.means[3 * (size_t)i + k] = gm[k];
-            p.out.scales[3 * (size_t)i + k] = gs[k];
-            p.out.normals[3 * (size_t)i + k] = gn[k];
+            const size_t o = 3 * (size_t)i + k;
+            p.out.means[o] = acc ? p.out.means[o] + gm[k] : gm[k];
+            p.out.scales[o] = acc ? p.out.scales[o] + gs[k] : gs[k];
+            p.out.normals[o] = acc ? p.out.normals[o] + gn[k] : gn[k];
         }
-        reinterpret_cast<float4 *>(p.out.quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-        p.out.opac1[i] = go1;
-        p.out.opac2[i] = go2;
+        float4 q4 = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        if (acc) {
+            const float4 o4 = reinterpret_cast<const float4 *>(p.out.quats)[i];
+            q4.x += o4.x; q4.y += o4.y; q4.z += o4.z; q4.w += o4.w;
+        }
+        reinterpret_cast<float4 *>(p.out.quats)[i] = q4;
+        p.out.opac1[i] = acc ? p.out.opac1[i] + go1 : go1;
+        p.out.opac2[i] = acc ? p.out.opac2[i] + go2 : go2;
     }
     __syncthreads();
     // SH gradients: shared rows -> contiguous global slice, coalesced
     float *dst = p.out.sh + (size_t)nc3 * base;
+    const bool acc = p.cfg.accumulate != 0;
     for (int j = threadIdx.x; j < rows * nc3; j += blockDim.x) {
         const int r = j / nc3, c = j - r * nc3;
-        dst[j] = gsh_s[r * shs + c];
+        dst[j] = acc ? dst[j] + gsh_s[r * shs + c] : gsh_s[r * shs + c];
     }
 }
 

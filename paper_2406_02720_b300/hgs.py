@@ -29,7 +29,7 @@ class HgsCamera(ctypes.Structure):
 
 class HgsConfig(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("batch", c_int), ("lowpass", c_float),
-                ("fov_clamp", c_int), ("plain", c_int), ("persistent", c_int)]
+                ("fov_clamp", c_int), ("plain", c_int), ("persistent", c_int), ("accumulate", c_int)]
 
 
 class HgsGaussians(ctypes.Structure):
@@ -200,7 +200,8 @@ STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd
 
 
 # ---- struct builders ----------------------------------------------------------------------
-def make_config(tile=(16, 16), batch=0, lowpass=0.3, fov_clamp=True, plain=False, persistent=False) -> HgsConfig:
+def make_config(tile=(16, 16), batch=0, lowpass=0.3, fov_clamp=True, plain=False, persistent=False,
+                accumulate=False) -> HgsConfig:
     c = HgsConfig()
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
     c.batch = int(batch)
@@ -208,6 +209,7 @@ def make_config(tile=(16, 16), batch=0, lowpass=0.3, fov_clamp=True, plain=False
     c.fov_clamp = 1 if fov_clamp else 0
     c.plain = 1 if plain else 0
     c.persistent = 1 if persistent else 0
+    c.accumulate = 1 if accumulate else 0
     return c
 
 

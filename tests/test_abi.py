@@ -76,6 +76,6 @@ def test_host_validation_rejects_bad_arguments():
 
 def test_camera_struct_layout_matches_header():
     assert ctypes.sizeof(H.HgsCamera) == 4 * (12 + 4 + 2 + 1 + 3)
-    assert ctypes.sizeof(H.HgsConfig) == 7 * 4
+    assert ctypes.sizeof(H.HgsConfig) == 8 * 4
     cams = H.make_cameras([scenes.config3_camera()])
     assert cams[0].width == 1920 and cams[0].viewmat[11] == np.float32(12.0)
