@@ -218,12 +218,12 @@ def run_gpu(args):
 
     # ---- work counters for the roofline (one extra forward, not timed) ------------------
     stats = rast.stats(dL)
-    roof = roofline(phases, stats, n_pairs, sc.n, clocks)
+    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks)
 
     # ---- end to end through host buffers --------------------------------------------------
     e2e = run_e2e(args, rast, g, dL, grads, step, pixels, dev)
 
-    launches = 9 + n_sort_passes(rast.total_tiles)     # project, scan, dup, hist, passes, ranges, fwd, bwd, proj_bwd
+    launches = launches_per_step(rast.total_tiles, persistent=bool(cfg.persistent))
     result = {
         "metric": METRIC, "value": aggregate_value(pixels, ws, ms_max), "unit": "Mpixel/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -235,10 +235,12 @@ def run_gpu(args):
                    "pairs": n_pairs, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
         "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
-        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, n_sort_passes(rast.total_tiles)),
+        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles),
         "clocks": clocks,
         "e2e": e2e, "gpu_launches": launches * args.steps,
     }
+    if args.sweep:
+        result["sweep"] = run_sweep(args, dev)
     if args.multiview:
         del step, fwd_step
         torch.cuda.empty_cache()
@@ -250,11 +252,44 @@ def run_gpu(args):
     return result if rank == 0 else None
 
 
-def n_sort_passes(total_tiles):
+def tile_bits(total_tiles):
     bits = 1
     while (1 << bits) < total_tiles:
         bits += 1
-    return (32 + bits + 7) // 8
+    return bits
+
+
+def n_sort_passes(total_tiles):
+    """8-bit radix passes: four over the per-splat depth keys, then ceil(tile bits / 8)
+    over the u32 tile ids of the depth-ordered pairs."""
+    return 4, (tile_bits(total_tiles) + 7) // 8
+
+
+def launches_per_step(total_tiles, persistent=False):
+    """Kernels of one fwd+bwd step: k_project; binning = k_depth_keys, 3 per radix
+    pass (k_upsweep, k_digit_scan, k_downsweep), k_scan, k_duplicate, k_ranges;
+    k_render_fwd (+ k_queue_count, k_queue_fill when persistent); k_render_bwd;
+    k_project_bwd."""
+    dp, tp = n_sort_passes(total_tiles)
+    return 1 + (1 + 3 * dp + 2 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 1
+
+
+def alg_bytes(n, n_pairs, total_tiles):
+    """Bytes each memory-bound phase must move in this design (per launch sequence):
+      project     : 252 B parameters read (mean 12, scale 12, quat 16, normal 12,
+                    opacities 8, SH 192) + 88 B written (record 64, depth 4, rect 16,
+                    tiles 4) per splat
+      bin         : per splat: depth keys 16 (read depth+tiles, write key+id), 4 depth
+                    passes x 20 (upsweep reads 4, downsweep reads 8 writes 8), scan 12
+                    (order, tiles, offset), duplicate 24 (order, offset, rect);
+                    per pair: 8 written by duplicate, 20 per tile pass, 4 read by ranges;
+                    8 per tile written by ranges
+      project_bwd : 252 B parameters + 48 B screen-space gradients read, 252 B written
+    """
+    dp, tp = n_sort_passes(total_tiles)
+    return {"project": n * (252 + 88),
+            "bin": n * (16 + 20 * dp + 12 + 24) + n_pairs * (8 + 20 * tp + 4) + total_tiles * 8,
+            "project_bwd": n * (252 + 48 + 252)}
 
 
 # Algorithmic operations per counted event of the compositing kernels, counted
@@ -276,7 +311,7 @@ def alu_work(stats, key):
     return fp32, mufu
 
 
-def roofline(phases, stats, n_pairs, n, clocks):
+def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     src = "of measured" if hbm else "of fallback"
@@ -303,25 +338,20 @@ def roofline(phases, stats, n_pairs, n, clocks):
                     "note": f"peak from 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz; algorithmic ops "
                             "= counted events x ops per event"})
     else:
-        bytes_per = {"project": n * (252 + 48 + 4 + 16 + 4), "project_bwd": n * (252 + 48 + 252),
-                     "bin": n_pairs * (12 + 8 + 24 * 6 + 8) + n * 8}
-        b = bytes_per.get(dom, 0)
+        b = alg_bytes(n, n_pairs, total_tiles).get(dom, 0)
         ach = b / (phases[dom] * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": None, "note": src})
     return out
 
 
-def phase_rooflines(phases, stats, n_pairs, n, n_passes):
+def phase_rooflines(phases, stats, n_pairs, n, total_tiles):
     """HBM fraction of the memory-bound phases and ALU fractions of the compositing
     phases (each against its own bound; algorithmic bytes/ops per launch)."""
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6400.0)
-    bytes_per = {"project": n * (252 + 48 + 4 + 16 + 4),
-                 "bin": n * (4 + 4 + 4 + 16 + 4) + n_pairs * (12 + 8 + 24 * n_passes + 8),
-                 "project_bwd": n * (252 + 48 + 252)}
     out = {}
-    for k, b in bytes_per.items():
+    for k, b in alg_bytes(n, n_pairs, total_tiles).items():
         out[k] = {"bound": "hbm", "GBs": b / (phases[k] * 1e-3) / 1e9, "frac": b / (phases[k] * 1e-3) / 1e9 / hbm}
     mhz = peaks.get("sm_max_mhz", 2032.0)
     for key, ph in (("fwd", "render_fwd"), ("bwd", "render_bwd")):
@@ -405,6 +435,36 @@ def run_multiview(args, dev):
             "images_identical": same, "status": st_b | st_p, "steps": args.mv_steps}
 
 
+# ---- stress sweep (disks with grazing planes, 100k..6M splats) --------------------------------
+def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_000)):
+    """fwd+bwd throughput curve over the splat count at 1920x1080, 30% 100:1 disks
+    with splitting planes within 5 degrees of the ray, plus the equal-opacity copy."""
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300 import scenes
+    from paper_2406_02720_b300.multiview import time_replays
+    from paper_2406_02720_b300.rasterizer import Gaussians, GraphStep, Rasterizer
+    out = []
+    runs = [(n, False) for n in sizes] + [(3_000_000, True)]
+    for n, equal in runs:
+        sc, cams = scenes.config5(n=n, equal_opacity=equal)
+        dL = torch.from_numpy(scenes.upstream_grad(105, cams)[0].reshape(-1)).to(dev)
+        g = Gaussians.from_scene(sc, dev)
+        r = Rasterizer(cams, n, H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch), device=dev)
+        r.forward(g)
+        r._alloc_pairs(int(r.num_pairs.item() * 1.05) + 4096)
+        grads = Gaussians.empty_like(g)
+        step = GraphStep(r, g, dL, grads)
+        ms = time_replays(step, args.sweep_steps)
+        st = r.read_status()
+        pix = cams[0].width * cams[0].height
+        out.append({"n": n, "equal_opacity": equal, "ms_per_step": ms, "Mpixel_per_s": pix / (ms * 1e3),
+                    "pairs": int(r.num_pairs.item()), "status": st})
+        del step, r, g, grads
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---- CPU oracle (reported baseline / reference arm) -----------------------------------------
 def cpu_baseline(args, n_tiles_sample=48, seed=5):
     """FP64 oracle on a bounded sample: full projection and projection adjoint of all
@@ -479,6 +539,8 @@ def main(argv=None):
     ap.add_argument("--mv-views", type=int, default=64)
     ap.add_argument("--mv-n", type=int, default=1_000_000)
     ap.add_argument("--mv-steps", type=int, default=10)
+    ap.add_argument("--sweep", action="store_true", help="also time the stress sweep (100k..6M splats)")
+    ap.add_argument("--sweep-steps", type=int, default=20)
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -120,10 +120,14 @@ typedef struct {
 } hgs_config;
 
 /* Per-(view, splat) projected records written by hgs_project, [n_views*n] rows.
- *   rec    [.,12] (16-B aligned): mu_x, mu_y, conic A, B, C, w'_x, w'_y,
- *                  alpha1, alpha2, r, g, b.  The conic is hat Sigma^-1 =
- *                  [[A,B],[B,C]]; w' = hat Sigma^-1 k / sqrt(2 v), so that the
- *                  half-plane fraction is P(d) = 1/2 erfc(-w'.d) (Eq. 8).
+ *   rec    [.,16] (16-B aligned): mu_x = ax + fx, mu_y = ay + fy with (ax, ay)
+ *                  integers and (fx, fy) the remainders (so the centre keeps
+ *                  ~1e-7 px accuracy anywhere in the image), then u11, u12, u22,
+ *                  w'_x, w'_y, alpha1, alpha2, r, g, b, 0, 0.  Layout:
+ *                  [ax, ay, fx, fy, u11, u12, u22, w'x, w'y, a1, a2, r, g, b, 0, 0].
+ *                  U = [[u11, u12], [0, u22]] is the Cholesky factor of the conic
+ *                  hat Sigma^-1 = U^T U; w' = hat Sigma^-1 k / sqrt(2 v), so that
+ *                  the half-plane fraction is P(d) = 1/2 erfc(-w'.d) (Eq. 8).
  *   depth  [.]     camera-space z of the mean (the sort key's low 32 bits)
  *   rect   [.,4]   (16-B aligned) covered tiles [x0,x1) x [y0,y1) of the view
  *   tiles  [.]     number of covered tiles, 0 if culled                       */

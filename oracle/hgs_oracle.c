@@ -582,19 +582,31 @@ static int eval_splat(const splats2d_t *s, int i, double px, double py, int plai
     return 1;
 }
 
-static void update_margin(double *margin, double val, double thr)
+
+/* Relative error of a GPU-side binary32 alpha from the position quantisation:
+ * mu-hat is held in binary32 (ulp 2^-23 |mu|), and log hat G moves by
+ * |conic d| per pixel of offset, so a ~= |conic d| * 2^-22 * max(|mu|, 1).   */
+static double position_sensitivity(const splats2d_t *s, int i, double dx, double dy)
 {
-    double m = fabs(val - thr) / thr;
-    if (m < *margin) *margin = m;
+    const double *Q = s->conic + 3 * i;
+    double gx = Q[0] * dx + Q[1] * dy, gy = Q[1] * dx + Q[2] * dy;
+    double mu = fmax(fmax(fabs(s->mu2[2 * i]), fabs(s->mu2[2 * i + 1])), 1.0);
+    return sqrt(gx * gx + gy * gy) * ldexp(mu, -22);
 }
+
+#define OR_DECISION_REL 1e-4   /* binary32 rounding of everything but the position */
 
 /* Renders the tiles selected by tile_mask (all if NULL).
  * image [3,H,W], T [H,W], n_contrib [H,W] (1 + list position of the last
  * composited splat, 0 if none), margin [H,W] (smallest relative distance of
  * any threshold decision to its threshold).  Optional (may be NULL):
- * margin_a [H,W] the same over the 1/255 floor and step-sign decisions only,
- * margin_T [H,W] over the 1e-4 transmittance stop only, n_comp [H,W] the number
- * of composited splats.                                                       */
+ * margin_a [H,W], margin_T [H,W]: the smallest distance of the 1/255-floor (and
+ * step-sign) decisions, resp. of the 1e-4 transmittance stop, to their
+ * thresholds, each divided by the relative error a binary32 evaluation can
+ * carry there (OR_DECISION_REL plus the position term above; for the stop, the
+ * sum of those errors over the composited splats).  A value <= 1 marks a
+ * decision binary32 arithmetic cannot be expected to reproduce.
+ * n_comp [H,W]: the number of composited splats.                              */
 int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic,
                   const double *wp, const double *rgb, const double *op1, const double *op2,
                   const uint32_t *ids, const uint32_t *ranges, const or_camera *cam,
@@ -616,28 +628,40 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
         for (int py = ty * o->tile_h; py < (ty + 1) * o->tile_h && py < H; ++py)
             for (int px = tx * o->tile_w; px < (tx + 1) * o->tile_w && px < W; ++px) {
                 double pcx = px + 0.5, pcy = py + 0.5;
-                double T = 1.0, C[3] = {0, 0, 0}, mga = 1e300, mgT = 1e300;
+                double T = 1.0, C[3] = {0, 0, 0}, mg = 1e300, mga = 1e300, mgT = 1e300;
+                double step_mg = 1e300, t_err = 0.0;
                 int last = 0, ncomp = 0;
                 for (uint32_t j = beg; j < end; ++j) {
                     int i = (int)ids[j];
                     if (mode[i] == OR_CULLED) continue;
                     eval_t e;
-                    if (!eval_splat(&s, i, pcx, pcy, o->plain, &e, &mga)) continue;
-                    update_margin(&mga, e.a, OR_ALPHA_MIN);
+                    if (!eval_splat(&s, i, pcx, pcy, o->plain, &e, &step_mg)) continue;
+                    double rel = fabs(e.a - OR_ALPHA_MIN) / OR_ALPHA_MIN;
+                    double sens = position_sensitivity(&s, i, pcx - mu2[2 * i], pcy - mu2[2 * i + 1]);
+                    if (rel < mg) mg = rel;
+                    double na = rel / (OR_DECISION_REL + sens);
+                    if (na < mga) mga = na;
                     if (e.a < OR_ALPHA_MIN) continue;
                     double Tn = T * (1.0 - e.a);
-                    update_margin(&mgT, Tn, OR_T_MIN);
+                    double relT = fabs(Tn - OR_T_MIN) / OR_T_MIN;
+                    if (relT < mg) mg = relT;
+                    double this_err = e.a / (1.0 - e.a) * sens;
+                    double nT = relT / (OR_DECISION_REL * (1.0 + ncomp / 100.0) + t_err + this_err);
+                    if (nT < mgT) mgT = nT;
                     if (Tn < OR_T_MIN) break;
                     for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * e.a * T;
                     T = Tn;
+                    t_err += this_err;
                     last = (int)(j - beg) + 1;
                     ncomp++;
                 }
+                if (step_mg < mg) mg = step_mg;
+                if (step_mg / OR_DECISION_REL < mga) mga = step_mg / OR_DECISION_REL;
                 size_t pix = (size_t)py * W + px;
                 for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = C[ch] + T * cam->bg[ch];
                 T_out[pix] = T;
                 n_contrib[pix] = last;
-                margin[pix] = mga < mgT ? mga : mgT;
+                margin[pix] = mg;
                 if (margin_a) margin_a[pix] = mga;
                 if (margin_T) margin_T[pix] = mgT;
                 if (n_comp) n_comp[pix] = ncomp;

@@ -43,6 +43,63 @@ __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); 
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 
+// ---- compensated binary32 arithmetic (value = hi + lo) ---------------------------
+// Used for the projected centre, which must be exact to ~1e-7 px although it is
+// near 2000 px: t = W mu + t_c, x/z and f x/z + c are formed from error-free
+// products (fma) and sums, then split into an integer anchor and a fraction.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_renorm(float hi, float lo) {   // |hi| >= |lo|
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    return df_renorm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF a, float b) {
+    const DF p = two_prod(a.hi, b);
+    return df_renorm(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF p = two_prod(q1, b.hi);
+    float r = __fsub_rn(a.hi, p.hi);
+    r = __fsub_rn(r, p.lo);
+    r = __fadd_rn(r, a.lo);
+    r = __fsub_rn(r, __fmul_rn(q1, b.lo));
+    return df_renorm(q1, __fdiv_rn(r, b.hi));
+}
+
+// Projected centre (anchor = nearest integer, fraction = rest), compensated.
+__device__ __forceinline__ void precise_centre(const float m[3], const hgs_camera &cam, float out[4]) {
+    const float *V = cam.viewmat;
+    DF t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        DF acc = two_prod(V[4 * i], m[0]);
+        acc = df_add(acc, two_prod(V[4 * i + 1], m[1]));
+        acc = df_add(acc, two_prod(V[4 * i + 2], m[2]));
+        t[i] = df_add(acc, DF{V[4 * i + 3], 0.0f});
+    }
+    const DF mx = df_add(df_mul(df_div(t[0], t[2]), cam.fx), DF{cam.cx, 0.0f});
+    const DF my = df_add(df_mul(df_div(t[1], t[2]), cam.fy), DF{cam.cy, 0.0f});
+    out[0] = rintf(mx.hi);
+    out[1] = rintf(my.hi);
+    out[2] = __fadd_rn(__fsub_rn(mx.hi, out[0]), mx.lo);
+    out[3] = __fadd_rn(__fsub_rn(my.hi, out[1]), my.lo);
+}
+
 struct Canon {
     bool culled;
     float depth, mux, muy, a, b, c, det;
@@ -526,10 +583,13 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
         sh_basis(deg, dx * il, dy * il, dz * il, Y);
         float rgb[3];
         sh_colour(sm, t, deg, Y, rgb);
-        float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 3 * vi;
-        rec[0] = make_float4(cb.mux, cb.muy, u11, u12);
-        rec[1] = make_float4(u22, h.wpx, h.wpy, o1);
-        rec[2] = make_float4(o2, fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f));
+        float ctr[4];
+        precise_centre(P.m, cam, ctr);
+        float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 4 * vi;
+        rec[0] = make_float4(ctr[0], ctr[1], ctr[2], ctr[3]);
+        rec[1] = make_float4(u11, u12, u22, h.wpx);
+        rec[2] = make_float4(h.wpy, o1, o2, fmaxf(rgb[0], 0.0f));
+        rec[3] = make_float4(fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), 0.0f, 0.0f);
     }
 }
 

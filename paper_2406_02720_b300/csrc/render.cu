@@ -82,27 +82,34 @@ struct Batch {
     uint32_t id[BATCH];
 };
 
+// Stages splat id into slot k.  The centre is made tile-local,
+// (anchor - tile origin) + fraction, so that pixel offsets are formed from small
+// numbers and stay exact to ~1e-7 px anywhere in the image.
 template <int BATCH>
-__device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH> &s, int k) {
-    const float4 r0 = __ldg(rec + 3 * (size_t)id);
-    const float4 r1 = __ldg(rec + 3 * (size_t)id + 1);
-    const float4 r2 = __ldg(rec + 3 * (size_t)id + 2);
-    s.mx[k] = r0.x;
-    s.my[k] = r0.y;
-    s.u11[k] = __fmul_rn(kUScale, r0.z);
-    s.u12[k] = __fmul_rn(kUScale, r0.w);
-    s.u22[k] = __fmul_rn(kUScale, r1.x);
-    s.wx[k] = r1.y;
-    s.wy[k] = r1.z;
-    const float a1 = r1.w, a2 = r2.x;
+__device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH> &s, int k,
+                                      float ox, float oy) {
+    const float4 r0 = __ldg(rec + 4 * (size_t)id);
+    const float4 r1 = __ldg(rec + 4 * (size_t)id + 1);
+    const float4 r2 = __ldg(rec + 4 * (size_t)id + 2);
+    const float4 r3 = __ldg(rec + 4 * (size_t)id + 3);
+    const float mx = __fadd_rn(__fsub_rn(r0.x, ox), r0.z);
+    const float my = __fadd_rn(__fsub_rn(r0.y, oy), r0.w);
+    s.mx[k] = mx;
+    s.my[k] = my;
+    s.u11[k] = __fmul_rn(kUScale, r1.x);
+    s.u12[k] = __fmul_rn(kUScale, r1.y);
+    s.u22[k] = __fmul_rn(kUScale, r1.z);
+    s.wx[k] = r1.w;
+    s.wy[k] = r2.x;
+    const float a1 = r2.y, a2 = r2.z;
     s.a2[k] = a2;
     s.da[k] = __fsub_rn(a1, a2);
     const float amax = fmaxf(a1, a2);
     // alpha <= amax * G < 1/255 whenever log2 G < -log2(255 amax); 1e-3 covers ex2/lg2 error
     s.qcut[k] = amax > 0.0f ? __fadd_rn(lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : -1.0f;
-    s.r[k] = r2.y;
-    s.g[k] = r2.z;
-    s.b[k] = r2.w;
+    s.r[k] = r2.w;
+    s.g[k] = r3.x;
+    s.b[k] = r3.y;
     s.id[k] = id;
     // |U~ d|^2 <= qcut is an ellipse with half-extents sqrt(qcut) * sqrt(diag((U~^T U~)^-1)):
     // hy = sqrt(qcut) / u22, hx = sqrt(qcut) * sqrt(1 + (u12/u22)^2) / u11.  Inflated so
@@ -113,10 +120,10 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
         const float ru = s.u12[k] / s.u22[k];
         const float hy = rq / s.u22[k] * 1.001f + 1e-3f;
         const float hx = rq * sqrtf(1.0f + ru * ru) / s.u11[k] * 1.001f + 1e-3f;
-        s.bxl[k] = r0.x - hx;
-        s.bxh[k] = r0.x + hx;
-        s.byl[k] = r0.y - hy;
-        s.byh[k] = r0.y + hy;
+        s.bxl[k] = mx - hx;
+        s.bxh[k] = mx + hx;
+        s.byl[k] = my - hy;
+        s.byh[k] = my + hy;
     } else {
         s.bxl[k] = s.byl[k] = 1e30f;
         s.bxh[k] = s.byh[k] = -1e30f;
@@ -224,8 +231,11 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
     warp_block<TW>(ti, TH, bx, by);
     const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < ti.W && py < ti.H;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    const float xl = (float)bx + 0.5f, xh = (float)bx + 7.5f, yl = (float)by + 0.5f, yh = (float)by + 3.5f;
+    // tile-local coordinates (pixel centres at i + 1/2)
+    const int ox = ti.tx * TW, oy = ti.ty * TH;
+    const float fox = (float)ox, foy = (float)oy;
+    const float fpx = (float)(px - ox) + 0.5f, fpy = (float)(py - oy) + 0.5f;
+    const float xl = (float)(bx - ox) + 0.5f, xh = xl + 7.0f, yl = (float)(by - oy) + 0.5f, yh = yl + 3.0f;
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
@@ -239,7 +249,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
             if (j < ti.end) {
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH>(rec, id, s, k);
+                stage<BATCH>(rec, id, s, k, fox, foy);
             }
         }
         __syncthreads();
@@ -320,8 +330,11 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
     warp_block<TW>(ti, TH, bx, by);
     const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < ti.W && py < ti.H;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    const float xl = (float)bx + 0.5f, xh = (float)bx + 7.5f, yl = (float)by + 0.5f, yh = (float)by + 3.5f;
+    // tile-local coordinates (pixel centres at i + 1/2)
+    const int ox = ti.tx * TW, oy = ti.ty * TH;
+    const float fox = (float)ox, foy = (float)oy;
+    const float fpx = (float)(px - ox) + 0.5f, fpy = (float)(py - oy) + 0.5f;
+    const float xl = (float)(bx - ox) + 0.5f, xh = xl + 7.0f, yl = (float)(by - oy) + 0.5f, yh = yl + 3.0f;
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
     const size_t HW = (size_t)ti.W * ti.H;
@@ -353,7 +366,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
             if (j < bend) {
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH>(rec, id, s, k);
+                stage<BATCH>(rec, id, s, k, fox, foy);
             }
         }
         __syncthreads();

@@ -84,7 +84,7 @@ class Rasterizer:
         self.total_tiles, self.total_pixels = H.hgs_layout(self.cams_host, self.n_views, self.cfg)
         vn = self.n * self.n_views
         f32, i32, dev = torch.float32, torch.int32, self.device
-        self.rec = torch.empty((vn, 12), dtype=f32, device=dev)
+        self.rec = torch.empty((vn, 16), dtype=f32, device=dev)
         self.depth = torch.empty(vn, dtype=f32, device=dev)
         self.rect = torch.empty((vn, 4), dtype=i32, device=dev)
         self.tiles = torch.empty(vn, dtype=i32, device=dev)

@@ -5,9 +5,10 @@ import numpy as np
 import oracle
 
 # A pixel whose oracle decisions (1/255 floor, step-mode sign) sit within this
-# relative distance of their threshold can flip between FP32 and FP64.  The 1e-4
-# stop compares a transmittance that carries the rounding of every composited
-# splat, so its margin grows with their number.
+# relative distance of their threshold can flip between FP32 and FP64.  The
+# oracle's margin_a / margin_T are this distance divided by the error a binary32
+# evaluation can carry (which includes the binary32 position of the splat and,
+# for the 1e-4 stop, the errors of every composited splat); <= 1 means exempt.
 EXEMPT_MARGIN = 1e-4
 
 
@@ -15,7 +16,9 @@ def exempt(ref):
     """Pixels whose threshold decisions FP32 cannot be expected to reproduce."""
     if "margin_a" not in ref:
         return ref["margin"] <= EXEMPT_MARGIN
-    return (ref["margin_a"] <= EXEMPT_MARGIN) | (ref["margin_T"] <= EXEMPT_MARGIN * (1.0 + ref["n_comp"] / 100.0))
+    return (ref["margin_a"] <= 1.0) | (ref["margin_T"] <= 1.0)
+
+
 IMAGE_ATOL = 1e-4
 # One threshold flip changes a pixel by at most about a/255-scale amounts; exempt
 # pixels must still agree to this bound.
@@ -39,7 +42,7 @@ def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persi
     out["keys"] = k.cpu().numpy().view(np.uint64)
     out["ids"] = i.cpu().numpy().view(np.uint32)
     out["ranges"] = r.ranges.cpu().numpy().view(np.uint32)
-    out["rec"] = r.rec.cpu().numpy().reshape(len(cams), sc.n, 12)
+    out["rec"] = r.rec.cpu().numpy().reshape(len(cams), sc.n, 16)
     out["depth"] = r.depth.cpu().numpy().reshape(len(cams), sc.n)
     out["rect"] = r.rect.cpu().numpy().reshape(len(cams), sc.n, 4)
     out["tiles"] = r.tiles.cpu().numpy().reshape(len(cams), sc.n)
@@ -54,7 +57,7 @@ def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persi
     return out
 
 
-def compare_image(gpu_img, gpu_T, gpu_nc, ref, atol=IMAGE_ATOL, max_exempt_frac=1e-2):
+def compare_image(gpu_img, gpu_T, gpu_nc, ref, atol=IMAGE_ATOL, max_exempt_frac=5e-2):
     """Max-abs image/T error on pixels away from threshold decisions; n_contrib equal there.
     Pixels with a decision within EXEMPT_MARGIN of its threshold (long lists make
     hundreds of decisions per pixel) are held to EXEMPT_ATOL only."""

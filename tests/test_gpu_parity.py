@@ -35,19 +35,23 @@ def test_projection_fields(cuda_ok, cfg1):
     vis = pr["tiles"] > 0
     assert np.array_equal(out["depth"][0].view(np.uint32), pr["depth"].view(np.uint32))
     assert np.array_equal(out["rect"][0][vis], pr["rect"][vis])
-    rec = out["rec"][0]
-    assert np.array_equal(rec[vis, 0:2].view(np.uint32), pr["canon_mu"][vis].view(np.uint32))
-    u11, u12, u22 = (rec[vis, j].astype(np.float64) for j in (2, 3, 4))
+    rec = out["rec"][0].astype(np.float64)
+    # centre = integer anchor + remainder, to ~1e-7 px of the FP64 centre
+    assert np.all(rec[vis, 0:2] == np.round(rec[vis, 0:2]))
+    mu = rec[vis, 0:2] + rec[vis, 2:4]
+    assert np.abs(mu - pr["mu2"][vis]).max() < 2e-6
+    assert np.abs(mu - pr["canon_mu"][vis]).max() < 1e-3      # and close to the binning centre
+    u11, u12, u22 = rec[vis, 4], rec[vis, 5], rec[vis, 6]
     Q = np.stack([u11 * u11, u11 * u12, u12 * u12 + u22 * u22], 1)     # conic = U^T U
     Qr = pr["conic"][vis]
-    assert np.all(np.abs(Q - Qr).max(1) <= 2e-4 * np.abs(Qr).max(1))
+    assert np.all(np.abs(Q - Qr).max(1) <= 2e-6 * np.abs(Qr).max(1))
     normal = pr["mode"][vis] == oracle.NORMAL
-    wp = rec[vis, 5:7].astype(np.float64)[normal]
+    wp = rec[vis, 7:9][normal]
     wr = pr["wp"][vis][normal]
-    assert np.all(np.abs(wp - wr).max(1) <= 1e-3 * np.maximum(np.abs(wr).max(1), 1e-3))
-    np.testing.assert_allclose(rec[vis, 9:12], pr["rgb"][vis], atol=2e-6)
-    np.testing.assert_array_equal(rec[vis, 7], sc.opac1[vis])
-    np.testing.assert_array_equal(rec[vis, 8], sc.opac2[vis])
+    assert np.all(np.abs(wp - wr).max(1) <= 1e-4 * np.maximum(np.abs(wr).max(1), 1e-3))
+    np.testing.assert_allclose(rec[vis, 11:14], pr["rgb"][vis], atol=2e-6)
+    np.testing.assert_array_equal(rec[vis, 9], sc.opac1[vis])
+    np.testing.assert_array_equal(rec[vis, 10], sc.opac2[vis])
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
