@@ -91,21 +91,29 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        with open(self.path) as f:
+            lines = f.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
-        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
-        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return summarize_clocks(lines)
+
+
+def summarize_clocks(lines):
+    """Median SM clock under load, the maximum clock and the throttle reasons seen
+    in nvidia-smi CSV rows (the FIELDS of ClockSampler, no header)."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+    load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+    return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
 
 
 # ---- GPU arm --------------------------------------------------------------------------------
@@ -466,61 +474,101 @@ def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_00
 
 
 # ---- CPU oracle (reported baseline / reference arm) -----------------------------------------
-def cpu_baseline(args, n_tiles_sample=48, seed=5):
-    """FP64 oracle on a bounded sample: full projection and projection adjoint of all
-    splats, compositing and its adjoint on a random sample of tiles; the full-frame
-    time is extrapolated by the tile fraction."""
+class OracleSample:
+    """A bounded sample of the fwd+bwd step for the FP64 oracle.  The per-splat phases
+    (projection, binning, projection adjoint) run on a seeded subset of m splats and
+    scale by n/m; compositing and its adjoint run on k seeded tiles of the full scene
+    (its projection is prepared once, untimed) and scale by tiles/k."""
+
+    def __init__(self, args, seed=5):
+        import oracle
+        self.oracle = oracle
+        self.sc, cams, self.dL = _scene(args)
+        self.cam = cams[0]
+        self.tile = (args.tile_w, args.tile_h)
+        tx, ty = oracle.grid(self.cam, self.tile)
+        self.n_tiles = tx * ty
+        self.rng = np.random.default_rng(seed)
+        self.tile_order = self.rng.permutation(self.n_tiles)
+        self.splat_order = self.rng.permutation(self.sc.n)
+        self.pr_full = oracle.project(self.sc, self.cam, self.tile)
+        self.g2_sub = None
+
+    def step(self, m, k):
+        """Runs the sample; returns (estimated full-step seconds, measured seconds)."""
+        o = self.oracle
+        m = max(1, min(m, self.sc.n))
+        k = max(1, min(k, self.n_tiles))
+        sub = self.sc.subset(np.sort(self.splat_order[:m]))
+        mask = np.zeros(self.n_tiles, np.uint8)
+        mask[self.tile_order[:k]] = 1
+        g2 = np.random.default_rng(m).normal(size=(m, 12))
+        # the sampled tiles' lists (binning is timed on the splat subset above)
+        tb = time.perf_counter()
+        bins = o.bin_pairs(self.pr_full, self.cam, self.tile, tile_mask=mask)
+        prep = time.perf_counter() - tb
+        t0 = time.perf_counter()
+        pr = o.project(sub, self.cam, self.tile)
+        t1 = time.perf_counter()
+        o.bin_pairs(pr, self.cam, self.tile)
+        t2 = time.perf_counter()
+        o.project_bwd(sub, self.cam, pr["mode"], g2, self.tile)
+        t3 = time.perf_counter()
+        out = o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
+        o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
+        t4 = time.perf_counter()
+        per_splat = (t3 - t0) * self.sc.n / m
+        per_tile = (t4 - t3) * self.n_tiles / k
+        del out
+        return per_splat + per_tile, t4 - t0 + prep
+
+    def describe(self, m, k):
+        return (f"projection, binning and projection adjoint of {m} of {self.sc.n} splats (seeded subset, "
+                f"scaled by n/m); compositing fwd+bwd of {k} of {self.n_tiles} tiles (seeded, scaled by the "
+                "tile fraction); FP64")
+
+
+def cpu_baseline(args, m=None, k=48):
+    """One bounded oracle sample of the bench workload (about 10-30 s of CPU work)."""
     import oracle
-    sc, cams, dL = _scene(args)
-    cam = cams[0]
-    tile = (args.tile_w, args.tile_h)
-    tx, ty = oracle.grid(cam, tile)
-    rng = np.random.default_rng(seed)
-    mask = np.zeros(tx * ty, np.uint8)
-    mask[rng.choice(tx * ty, n_tiles_sample, replace=False)] = 1
-    t0 = time.perf_counter()
-    pr = oracle.project(sc, cam, tile)
-    t1 = time.perf_counter()
-    bins = oracle.bin_pairs(pr, cam, tile, tile_mask=mask)
-    t2 = time.perf_counter()
-    out = oracle.render(sc, cam, tile=tile, tile_mask=mask, proj=pr, bins=bins)
-    t3 = time.perf_counter()
-    g = oracle.render_bwd(sc, cam, dL, tile=tile, tile_mask=mask, proj=pr, bins=bins)
-    t4 = time.perf_counter()
-    frac = n_tiles_sample / float(tx * ty)
-    t_proj, t_bin, t_fwd, t_bwd_all = t1 - t0, t2 - t1, t3 - t2, t4 - t3
-    # render_bwd includes the projection adjoint of every splat; time it apart
-    t5 = time.perf_counter()
-    oracle.project_bwd(sc, cam, pr["mode"], g["grad2d"], tile)
-    t_pbwd = time.perf_counter() - t5
-    t_rbwd = max(t_bwd_all - t_pbwd, 0.0)
-    est = t_proj + t_bin + (t_fwd + t_rbwd) / frac + t_pbwd
-    pixels = cam.width * cam.height
+    samp = OracleSample(args)
+    m = m or samp.sc.n
+    est, meas = samp.step(m, k)
+    pixels = samp.cam.width * samp.cam.height
     return {"value": pixels / (est * 1e6), "unit": "Mpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n_tiles_sample} of {tx * ty} tiles (seeded) composited fwd+bwd in FP64; projection and "
-                      f"its adjoint over all {sc.n} splats; full-frame time extrapolated by the tile fraction",
-            "est_frame_s": est, "measured_s": t4 - t0 + t_pbwd}
+            "sample": samp.describe(m, k), "est_frame_s": est, "measured_s": meas}
 
 
 def run_reference(args):
+    """The FP64 oracle timed as the reference arm: every step is a bounded sample of
+    the bench workload, sized so that warm-up + steps take about two minutes."""
+    import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
         return None
+    samp = OracleSample(args)
+    budget = min(20.0, max(0.05, 120.0 / (args.steps + args.warmup)))
+    m, k = 20_000, 2
+    for _ in range(max(args.warmup, 1)):       # calibration: grow or shrink the sample to the budget
+        _, meas = samp.step(m, k)
+        scale = budget / max(meas, 1e-3)
+        m = int(min(samp.sc.n, max(2_000, m * scale)))
+        k = int(min(samp.n_tiles, max(1, k * scale)))
     vals = []
-    last = None
-    for _ in range(args.warmup):
-        cpu_baseline(args, n_tiles_sample=8)
     for _ in range(args.steps):
-        last = cpu_baseline(args, n_tiles_sample=8)
-        vals.append(last["value"])
-    v = statistics.mean(vals)
+        est, _ = samp.step(m, k)
+        vals.append(est)
+    est = statistics.mean(vals)
+    pixels = samp.cam.width * samp.cam.height
+    v = pixels / (est * 1e6)
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": (1920 * 1080) / (v * 1e3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"config3: {args.n} half-Gaussians, SH degree 3, 1920x1080, "
-                                                        "1 view, fwd+bwd (FP64 CPU oracle, sampled tiles)"},
-            "cpu_baseline": {"value": v, "unit": "Mpixel/s", "kind": "oracle", "cores": last["cores"],
-                             "sample": last["sample"]},
+            "data": "synthetic",
+            "config": {"workload": f"config3: {samp.sc.n} half-Gaussians, SH degree 3, "
+                                   f"{samp.cam.width}x{samp.cam.height}, 1 view, fwd+bwd (FP64 CPU oracle, sampled)"},
+            "cpu_baseline": {"value": v, "unit": "Mpixel/s", "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": samp.describe(m, k)},
             "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -213,18 +213,16 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
                 proj=proj, bins=bins)
 
 
-def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
-               tile_mask=None, proj=None, bins=None):
-    """FP64 adjoint of `render` for the loss L = sum(dL_dimage * image).
-
-    Returns the parameter gradients and the per-splat screen-space gradients
-    grad2d [N,12] (fields G2D_FIELDS)."""
+def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
+                  tile_mask=None, proj=None, bins=None):
+    """FP64 adjoint of the compositing alone (Eq. 10 blending, back to front) for the
+    loss L = sum(dL_dimage * image): the per-splat screen-space gradients grad2d
+    [N,12] (fields G2D_FIELDS)."""
     if proj is None:
         proj = project(sc, cam, tile, lowpass, fov_clamp)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
-    s = _scene64(sc)
-    n = s["means"].shape[0]
+    n = sc.n
     o = make_opts(tile, sc.sh_degree, lowpass, plain, fov_clamp)
     c = make_camera(cam)
     g2 = np.zeros((n, 12))
@@ -241,6 +239,20 @@ def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_
                         _p(proj["wp"], dp), _p(proj["rgb"], dp), _p(proj["opac1"], dp),
                         _p(proj["opac2"], dp), _p(ids, c_uint32), _p(bins["ranges"], c_uint32),
                         ctypes.byref(c), ctypes.byref(o), mask_p, _p(dLd, dp), _p(g2, dp))
+    return g2
+
+
+def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
+               tile_mask=None, proj=None, bins=None):
+    """FP64 adjoint of `render` for the loss L = sum(dL_dimage * image).
+
+    Returns the parameter gradients and the per-splat screen-space gradients
+    grad2d [N,12] (fields G2D_FIELDS)."""
+    if proj is None:
+        proj = project(sc, cam, tile, lowpass, fov_clamp)
+    if bins is None:
+        bins = bin_pairs(proj, cam, tile, tile_mask)
+    g2 = rasterize_bwd(sc, cam, dL_dimage, tile, lowpass, plain, fov_clamp, tile_mask, proj, bins)
     grads = project_bwd(sc, cam, proj["mode"], g2, tile, lowpass, fov_clamp)
     grads["grad2d"] = g2
     return grads
