@@ -222,7 +222,7 @@ def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, f
         proj = project(sc, cam, tile, lowpass, fov_clamp)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
-    n = sc.n
+    n = int(np.asarray(proj["mode"]).shape[0])
     o = make_opts(tile, sc.sh_degree, lowpass, plain, fov_clamp)
     c = make_camera(cam)
     g2 = np.zeros((n, 12))
