@@ -130,12 +130,18 @@ typedef struct {
  *                  the half-plane fraction is P(d) = 1/2 erfc(-w'.d) (Eq. 8).
  *   depth  [.]     camera-space z of the mean (the sort key's low 32 bits)
  *   rect   [.,4]   (16-B aligned) covered tiles [x0,x1) x [y0,y1) of the view
- *   tiles  [.]     number of covered tiles, 0 if culled                       */
+ *   tiles  [.]     number of covered tiles, 0 if culled
+ *   fp64_list [1 + n_views*n] uint32 scratch: hgs_project gathers here the
+ *                  (view, splat) records whose splitting plane nearly contains
+ *                  the ray (v < 1e-3 var_s) and recomputes their half-plane terms
+ *                  in FP64 in a second kernel.  Contents are not meaningful to
+ *                  the caller; hgs_render_bwd reuses it for the same purpose.     */
 typedef struct {
     float *rec;
     float *depth;
     int32_t *rect;
     uint32_t *tiles;
+    uint32_t *fp64_list;
 } hgs_proj;
 
 /* ---- sizes ------------------------------------------------------------- */
@@ -159,9 +165,10 @@ size_t hgs_render_workspace_size(const hgs_camera *cams_host, int n_views, const
  * hat Sigma = top-left 2x2 of J W Sigma^w W^T J^T (Eq. 3-5) plus the low-pass,
  * its inverse (the conic), mu-hat, the 3-sigma tile rect and the half-plane
  * terms of Eq. 7-8 (w'), and the SH colour.  Binning fields follow a fixed FP32
- * operation order without fused multiply-adds.  Near-degenerate splats
- * (ill-conditioned hat Sigma or a splitting plane nearly containing the ray)
- * have their conic and half-plane terms recomputed in FP64.
+ * operation order without fused multiply-adds.  Splats whose splitting plane
+ * nearly contains the ray (v < 1e-3 var_s, where the half-plane variance v
+ * loses most of its FP32 digits) have their half-plane terms recomputed in FP64
+ * by a second kernel over the list gathered in proj->fp64_list.
  * cams_host: host copy (sizes); cams_dev: the same cameras in device memory. */
 hgs_status hgs_project(const hgs_gaussians *g, const hgs_camera *cams_host,
                        const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
@@ -244,11 +251,13 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids,
 
 /* Chain rule from grad2d through Eq. 8, Eq. 3-5, Eq. 2 and the SH colour to
  * every parameter, summed over views.  Writes every entry of `out` (adds into
- * it when cfg->accumulate is set). */
+ * it when cfg->accumulate is set).  Near-degenerate (view, splat) pairs (as in
+ * hgs_project) take the FP64 adjoint in a second kernel; fp64_list is their
+ * [1 + n_views*n] uint32 scratch list. */
 hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host,
                            const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                            const float *grad2d, const hgs_gaussian_grads *out,
-                           int *dev_status, void *stream);
+                           uint32_t *fp64_list, int *dev_status, void *stream);
 
 /* hgs_rasterize_bwd followed by hgs_project_bwd; grad2d is caller scratch. */
 hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const uint32_t *ids,

@@ -72,11 +72,11 @@ bool gaussians_ok(const hgs_gaussians *g) {
            aligned16(g->sh);
 }
 
-bool proj_ok(const hgs_proj *p, long long vn) {
+bool proj_ok(const hgs_proj *p, long long vn, bool need_list = false) {
     if (!p) return false;
     if (vn == 0) return true;
-    return p->rec && p->depth && p->rect && p->tiles && aligned16(p->rec) && aligned16(p->rect) &&
-           aligned16(p->tiles);
+    return p->rec && p->depth && p->rect && p->tiles && (p->fp64_list || !need_list) && aligned16(p->rec) &&
+           aligned16(p->rect) && aligned16(p->tiles);
 }
 
 hgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HGS_OK : HGS_ERR_CUDA; }
@@ -126,7 +126,7 @@ hgs_status hgs_project(const hgs_gaussians *g, const hgs_camera *cams_host, cons
     ViewTable vt;
     hgs_status st = build_views(cams_host, n_views, cfg, &vt);
     if (st != HGS_OK) return st;
-    if (!gaussians_ok(g) || !cams_dev || !proj_ok(out, (long long)g->n * n_views)) return HGS_ERR_INVALID;
+    if (!gaussians_ok(g) || !cams_dev || !proj_ok(out, (long long)g->n * n_views, true)) return HGS_ERR_INVALID;
     ProjLaunch p;
     p.g = *g;
     p.cams = cams_dev;
@@ -250,13 +250,14 @@ hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, co
 
 hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host, const hgs_camera *cams_dev,
                            int n_views, const hgs_config *cfg, const float *grad2d, const hgs_gaussian_grads *out,
-                           int *dev_status, void *stream) {
+                           uint32_t *fp64_list, int *dev_status, void *stream) {
     ViewTable vt;
     hgs_status st = build_views(cams_host, n_views, cfg, &vt);
     if (st != HGS_OK) return st;
     if (!gaussians_ok(g) || !cams_dev || !out) return HGS_ERR_INVALID;
     if (g->n > 0 && (!grad2d || !aligned16(grad2d) || !out->means || !out->scales || !out->quats ||
-                     !out->normals || !out->opac1 || !out->opac2 || !out->sh || !aligned16(out->quats)))
+                     !out->normals || !out->opac1 || !out->opac2 || !out->sh || !aligned16(out->quats) ||
+                     !fp64_list))
         return HGS_ERR_INVALID;
     ProjBwdLaunch p;
     p.g = *g;
@@ -265,6 +266,7 @@ hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host, 
     p.cfg = *cfg;
     p.grad2d = grad2d;
     p.out = *out;
+    p.fp64_list = fp64_list;
     p.status = dev_status;
     return cuda_status(launch_project_bwd(p, static_cast<cudaStream_t>(stream)));
 }
@@ -278,7 +280,7 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
     hgs_status st = hgs_rasterize_bwd(proj, g->n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes,
                                       final_T, n_contrib, dL_dimage, grad2d, dev_status, stream);
     if (st != HGS_OK) return st;
-    return hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, dev_status, stream);
+    return hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, proj->fp64_list, dev_status, stream);
 }
 
 }  // extern "C"

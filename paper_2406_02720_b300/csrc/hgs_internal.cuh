@@ -77,6 +77,7 @@ struct ProjBwdLaunch {
     hgs_config cfg;
     const float *grad2d;
     hgs_gaussian_grads out;
+    uint32_t *fp64_list;
     int *status;
 };
 cudaError_t launch_project_bwd(const ProjBwdLaunch &p, cudaStream_t s);

@@ -490,9 +490,38 @@ struct HalfPlane {
     float wpx, wpy;
 };
 
+// Appends a (view, splat) index to a list [count, entries...] with one atomic per
+// warp.  Used to gather the rare near-degenerate splats, so that their FP64 work
+// runs in full warps in a follow-up kernel instead of stalling a warp of
+// FP32 splats on one lane (FP64 issues at a small fraction of the FP32 rate).
+__device__ __forceinline__ void list_append(uint32_t *list, bool want, uint32_t value) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(list, (uint32_t)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    if (want) list[1 + base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+__device__ __forceinline__ Params load_params(const hgs_gaussians &g, int i) {
+    Params P;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        P.m[k] = g.means[3 * (size_t)i + k];
+        P.s[k] = g.scales[3 * (size_t)i + k];
+        P.n[k] = g.normals[3 * (size_t)i + k];
+    }
+    const float4 q4 = reinterpret_cast<const float4 *>(g.quats)[i];
+    P.q[0] = q4.x; P.q[1] = q4.y; P.q[2] = q4.z; P.q[3] = q4.w;
+    return P;
+}
+
 // FP64 recomputation of the half-plane terms of a splat whose plane nearly
-// contains the ray (rare; kept out of line so the FP32 path keeps its registers).
-__device__ __noinline__ HalfPlane half_plane_fp64(Params P, const hgs_camera &cam, float lp, int fov_clamp) {
+// contains the ray.
+__device__ __forceinline__ HalfPlane half_plane_fp64(const Params &P, const hgs_camera &cam, float lp, int fov_clamp) {
     Proj<double> d;
     d.run(P.m, P.s, P.q, P.n, cam, lp, fov_clamp);
     HalfPlane h;
@@ -525,6 +554,7 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
     const float lp = p.cfg.lowpass;
 
     for (int v = 0; v < p.n_views; ++v) {
+        bool defer = false;
         const hgs_camera &cam = p.cams[v];
         const size_t vi = (size_t)v * n + i;
         Canon cb;
@@ -561,7 +591,7 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
             const float trip = dot3(u, cr);
             const float vv = (trip * trip + lp * (dot3(up0, up0) + dot3(up1, up1)) + lp * lp * var_s) * id;
             if (vv < kVRelFp64 * var_s) {
-                h = half_plane_fp64(P, cam, lp, p.cfg.fov_clamp);
+                defer = true;          // w' is written by k_project_fp64
             } else {
                 const float sc = rsqrtf(2.0f * vv);
                 h.mode = MODE_NORMAL;
@@ -590,6 +620,20 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
         rec[1] = make_float4(u11, u12, u22, h.wpx);
         rec[2] = make_float4(h.wpy, o1, o2, fmaxf(rgb[0], 0.0f));
         rec[3] = make_float4(fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), 0.0f, 0.0f);
+        list_append(p.out.fp64_list, defer, (uint32_t)vi);
+    }
+}
+
+// Half-plane terms of the gathered near-degenerate (view, splat) records, FP64.
+__global__ void __launch_bounds__(kProjBlock) k_project_fp64(ProjLaunch p) {
+    const uint32_t cnt = min(p.out.fp64_list[0], (uint32_t)p.n_views * (uint32_t)p.g.n);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const uint32_t vi = p.out.fp64_list[1 + e];
+        const int v = (int)(vi / (uint32_t)p.g.n), i = (int)(vi - (uint32_t)v * (uint32_t)p.g.n);
+        const Params P = load_params(p.g, i);
+        const HalfPlane h = half_plane_fp64(P, p.cams[v], p.cfg.lowpass, p.cfg.fov_clamp);
+        p.out.rec[16 * (size_t)vi + 7] = h.wpx;
+        p.out.rec[16 * (size_t)vi + 8] = h.wpy;
     }
 }
 
@@ -701,8 +745,9 @@ struct Grads {
     float m[3], s[3], q[4], n[3];
 };
 
-// FP64 adjoint of the projection of one near-degenerate splat (rare, out of line).
-__device__ __noinline__ Grads proj_vjp_fp64(Params P, const hgs_camera &cam, float lp, int fov_clamp, G2 g2) {
+// FP64 adjoint of the projection of one near-degenerate splat.
+__device__ __forceinline__ Grads proj_vjp_fp64(const Params &P, const hgs_camera &cam, float lp, int fov_clamp,
+                                               const G2 &g2) {
     Proj<double> d;
     d.run(P.m, P.s, P.q, P.n, cam, lp, fov_clamp);
     Grads r;
@@ -751,15 +796,9 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) 
             go2 += g2.v[8];
             Proj<float> f;
             f.run(P.m, P.s, P.q, P.n, cam, lp, p.cfg.fov_clamp);
-            if (f.degenerate()) {
-                const Grads r = proj_vjp_fp64(P, cam, lp, p.cfg.fov_clamp, g2);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { gm[k] += r.m[k]; gs[k] += r.s[k]; gn[k] += r.n[k]; }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) gq[k] += r.q[k];
-            } else {
-                proj_vjp<float>(f, P.s, cam, g2.v, gm, gs, gq, gn);
-            }
+            const bool defer = f.degenerate();     // geometry adjoint by k_project_bwd_fp64
+            list_append(p.fp64_list, defer, (uint32_t)vi);
+            if (!defer) proj_vjp<float>(f, P.s, cam, g2.v, gm, gs, gq, gn);
             // SH colour: rgb = max(0, sum c Y(dir) + 1/2), dir = unit(mu - camera centre)
             float cpos[3];
             camera_centre(cam, cpos);
@@ -818,33 +857,65 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) 
     }
 }
 
+// Geometry adjoint (mean, scale, quaternion, normal) of the gathered near-degenerate
+// (view, splat) pairs in FP64, added to what k_project_bwd wrote.  Atomic adds,
+// since one splat can be listed for several views.
+__global__ void __launch_bounds__(kProjBlock) k_project_bwd_fp64(ProjBwdLaunch p) {
+    const uint32_t cnt = min(p.fp64_list[0], (uint32_t)p.n_views * (uint32_t)p.g.n);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const uint32_t vi = p.fp64_list[1 + e];
+        const int v = (int)(vi / (uint32_t)p.g.n), i = (int)(vi - (uint32_t)v * (uint32_t)p.g.n);
+        const Params P = load_params(p.g, i);
+        G2 g2;
+        const float4 *g4 = reinterpret_cast<const float4 *>(p.grad2d) + 3 * (size_t)vi;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float4 a = g4[j];
+            g2.v[4 * j] = a.x; g2.v[4 * j + 1] = a.y; g2.v[4 * j + 2] = a.z; g2.v[4 * j + 3] = a.w;
+        }
+        const Grads r = proj_vjp_fp64(P, p.cams[v], p.cfg.lowpass, p.cfg.fov_clamp, g2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(p.out.means + 3 * (size_t)i + k, r.m[k]);
+            atomicAdd(p.out.scales + 3 * (size_t)i + k, r.s[k]);
+            atomicAdd(p.out.normals + 3 * (size_t)i + k, r.n[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(p.out.quats + 4 * (size_t)i + k, r.q[k]);
+    }
+}
+
 }  // namespace
 
 size_t project_smem_bytes(bool bwd) {
     return sizeof(StageSmem) + (bwd ? sizeof(float) * kShStride3 * kProjBlock : 0);
 }
 
+// Grid of the FP64 follow-up kernels: the list length is known only on the device,
+// so a fixed grid strides over it (one thread per entry while it is short).
+constexpr int kFp64Blocks = 148;
+
 cudaError_t launch_project(const ProjLaunch &p, cudaStream_t s) {
     if (p.g.n == 0) return cudaSuccess;
-    static bool attr = false;
     const size_t smem = project_smem_bytes(false);
-    if (!attr) {
-        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.out.fp64_list, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     k_project<<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_project_fp64<<<kFp64Blocks, kProjBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project_bwd(const ProjBwdLaunch &p, cudaStream_t s) {
     if (p.g.n == 0) return cudaSuccess;
-    static bool attr = false;
     const size_t smem = project_smem_bytes(true);
-    if (!attr) {
-        cudaFuncSetAttribute(k_project_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_project_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.fp64_list, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     k_project_bwd<<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_project_bwd_fp64<<<kFp64Blocks, kProjBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -44,7 +44,8 @@ class HgsGaussianGrads(ctypes.Structure):
 
 
 class HgsProj(ctypes.Structure):
-    _fields_ = [("rec", c_void_p), ("depth", c_void_p), ("rect", c_void_p), ("tiles", c_void_p)]
+    _fields_ = [("rec", c_void_p), ("depth", c_void_p), ("rect", c_void_p), ("tiles", c_void_p),
+                ("fp64_list", c_void_p)]
 
 
 class HgsError(RuntimeError):
@@ -92,7 +93,7 @@ def lib():
                                         c_size_t, vp, vp, vp, vp, vp, vp]
         L.hgs_project_bwd.restype = c_int
         L.hgs_project_bwd.argtypes = [POINTER(HgsGaussians), _CAM_P, vp, c_int, _CFG_P, vp,
-                                      POINTER(HgsGaussianGrads), vp, vp]
+                                      POINTER(HgsGaussianGrads), vp, vp, vp]
         L.hgs_render_stats.restype = c_int
         L.hgs_render_stats.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp, c_size_t,
                                        vp, vp, vp, vp, vp, vp, vp, vp]
@@ -177,9 +178,9 @@ def hgs_rasterize_bwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, w
                                    dev_status, stream), "hgs_rasterize_bwd")
 
 
-def hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, dev_status, stream):
+def hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, fp64_list, dev_status, stream):
     _check(lib().hgs_project_bwd(ctypes.byref(g), cams_host, cams_dev, n_views, ctypes.byref(cfg), grad2d,
-                                 ctypes.byref(out), dev_status, stream), "hgs_project_bwd")
+                                 ctypes.byref(out), fp64_list, dev_status, stream), "hgs_project_bwd")
 
 
 def hgs_render_bwd(g, proj, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, final_T, n_contrib,

@@ -88,6 +88,7 @@ class Rasterizer:
         self.depth = torch.empty(vn, dtype=f32, device=dev)
         self.rect = torch.empty((vn, 4), dtype=i32, device=dev)
         self.tiles = torch.empty(vn, dtype=i32, device=dev)
+        self.fp64_list = torch.empty(vn + 1, dtype=i32, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.ranges = torch.empty((self.total_tiles, 2), dtype=i32, device=dev)
@@ -114,6 +115,7 @@ class Rasterizer:
     def proj_struct(self) -> H.HgsProj:
         p = H.HgsProj()
         p.rec, p.depth, p.rect, p.tiles = _vp(self.rec), _vp(self.depth), _vp(self.rect), _vp(self.tiles)
+        p.fp64_list = _vp(self.fp64_list)
         return p
 
     def _stream(self):
@@ -142,7 +144,7 @@ class Rasterizer:
 
     def project_bwd(self, g: Gaussians, out: Gaussians):
         H.hgs_project_bwd(g.c_struct(), self.cams_host, _vp(self.cams_dev), self.n_views, self.cfg,
-                          _vp(self.grad2d), out.c_grads(), _vp(self.status), self._stream())
+                          _vp(self.grad2d), out.c_grads(), _vp(self.fp64_list), _vp(self.status), self._stream())
 
     # -- composite steps ---------------------------------------------------------------
     def forward_async(self, g: Gaussians):

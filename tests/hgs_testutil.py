@@ -46,6 +46,8 @@ def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persi
     out["depth"] = r.depth.cpu().numpy().reshape(len(cams), sc.n)
     out["rect"] = r.rect.cpu().numpy().reshape(len(cams), sc.n, 4)
     out["tiles"] = r.tiles.cpu().numpy().reshape(len(cams), sc.n)
+    fl = r.fp64_list.cpu().numpy().view(np.uint32)
+    out["fp64_fwd"] = np.sort(fl[1:1 + fl[0]])       # (view, splat) records given the FP64 half-plane path
     if dL is not None:
         flat = np.concatenate([np.asarray(d, np.float32).reshape(-1) for d in dL])
         dl = torch.from_numpy(flat).cuda()

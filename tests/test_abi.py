@@ -65,10 +65,15 @@ def test_host_validation_rejects_bad_arguments():
                    H.HGS_MAX_PAIRS + 1, ctypes.c_void_p(256), ctypes.c_void_p(256), ctypes.c_void_p(256),
                    ctypes.c_void_p(256), None, None)
     assert st == H.HGS_ERR_INVALID
-    # misaligned record buffer
-    p.rec = ctypes.c_void_p(260)
+    # projection without its FP64 scratch list
     g.n, g.sh_degree = 10, 0
     g.means = g.scales = g.quats = g.normals = g.opac1 = g.opac2 = g.sh = ctypes.c_void_p(256)
+    st = L.hgs_project(ctypes.byref(g), cams, ctypes.c_void_p(16), 1, ctypes.byref(cfg), ctypes.byref(p),
+                       None, None)
+    assert st == H.HGS_ERR_INVALID
+    # misaligned record buffer
+    p.fp64_list = ctypes.c_void_p(256)
+    p.rec = ctypes.c_void_p(260)
     st = L.hgs_project(ctypes.byref(g), cams, ctypes.c_void_p(16), 1, ctypes.byref(cfg), ctypes.byref(p),
                        None, None)
     assert st == H.HGS_ERR_INVALID

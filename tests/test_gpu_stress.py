@@ -24,6 +24,21 @@ def test_grazing_disks_against_oracle(cuda_ok):
     assert (ratio < 1e-3).sum() >= 20
     dL = masked_upstream(scenes.upstream_grad(105, cams), [ref])
     out = gpu_render(sc, cams, dL=dL)
+    # the gathered FP64 list is the set of drawn splats with v < 1e-3 var_s (the GPU
+    # decides in FP32, so only splats near the 1e-3 boundary may differ), and their
+    # half-plane terms are the FP64 ones
+    drawn = vis & (pr["tiles"] > 0)
+    r_all = pr["var_terms"][:, 1] / np.maximum(pr["var_terms"][:, 0], 1e-300)
+    want = np.flatnonzero(drawn & (pr["mode"] == oracle.NORMAL) & (r_all < 1e-3))
+    got = out["fp64_fwd"].astype(np.int64)
+    assert len(np.unique(got)) == len(got)
+    diff = np.setxor1d(got, want)
+    assert np.all(np.abs(r_all[diff] / 1e-3 - 1.0) < 1e-2), diff[:10]
+    assert len(got) >= 20
+    both = np.intersect1d(got, want)
+    wp = out["rec"][0][both][:, 7:9].astype(np.float64)
+    wr = pr["wp"][both]
+    assert np.all(np.abs(wp - wr).max(1) <= 1e-5 * np.abs(wr).max(1)), np.abs(wp - wr).max()
     assert np.array_equal(out["keys"], ref["bins"]["keys"])
     assert np.array_equal(out["ids"], ref["bins"]["ids"])
     compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
