@@ -469,20 +469,34 @@ __device__ __forceinline__ Params read_params(const StageSmem &sm, int t) {
     return P;
 }
 
-// SH colour (before the clamp) from the staged coefficients of thread t.
-__device__ __forceinline__ void sh_colour(const StageSmem &sm, int t, int deg, const float Y[16], float out[3]) {
-    const float *c = sm.sh + t * sh_stride(deg);
-    const int nc = (deg + 1) * (deg + 1);
-    float r = 0.0f, g = 0.0f, b = 0.0f;
+// SH colour (before the clamp) from the staged coefficients of thread t.  Degree 3
+// rows (48 floats at stride 52) are read as twelve 128-bit loads, which consecutive
+// threads take from distinct banks; entry j of a row is coefficient j / 3 of
+// channel j % 3.
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const StageSmem &sm, int t, const float Y[16], float out[3]) {
+    constexpr int nc = (DEG + 1) * (DEG + 1);
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    if (DEG == 3) {
+        const float4 *c4 = reinterpret_cast<const float4 *>(sm.sh + t * kShStride3);
 #pragma unroll
-    for (int l = 0; l < 16; ++l) {
-        if (l < nc) {
-            r += c[3 * l] * Y[l];
-            g += c[3 * l + 1] * Y[l];
-            b += c[3 * l + 2] * Y[l];
+        for (int q = 0; q < 12; ++q) {
+            const float4 c = c4[q];
+            acc[(4 * q) % 3] += c.x * Y[(4 * q) / 3];
+            acc[(4 * q + 1) % 3] += c.y * Y[(4 * q + 1) / 3];
+            acc[(4 * q + 2) % 3] += c.z * Y[(4 * q + 2) / 3];
+            acc[(4 * q + 3) % 3] += c.w * Y[(4 * q + 3) / 3];
+        }
+    } else {
+        const float *c = sm.sh + t * (3 * nc);
+#pragma unroll
+        for (int l = 0; l < nc; ++l) {
+            acc[0] += c[3 * l] * Y[l];
+            acc[1] += c[3 * l + 1] * Y[l];
+            acc[2] += c[3 * l + 2] * Y[l];
         }
     }
-    out[0] = r + 0.5f; out[1] = g + 0.5f; out[2] = b + 0.5f;
+    out[0] = acc[0] + 0.5f; out[1] = acc[1] + 0.5f; out[2] = acc[2] + 0.5f;
 }
 
 struct HalfPlane {
@@ -538,7 +552,8 @@ __device__ __forceinline__ HalfPlane half_plane_fp64(const Params &P, const hgs_
     return h;
 }
 
-__global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock, 5) k_project(ProjLaunch p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem &sm = *reinterpret_cast<StageSmem *>(smem_raw);
     const int n = p.g.n;
@@ -550,7 +565,6 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
     const int i = base + t;
     const Params P = read_params(sm, t);
     const float o1 = sm.o1[t], o2 = sm.o2[t];
-    const int deg = p.g.sh_degree;
     const float lp = p.cfg.lowpass;
 
     for (int v = 0; v < p.n_views; ++v) {
@@ -610,9 +624,9 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
         const float dx = P.m[0] - cpos[0], dy = P.m[1] - cpos[1], dz = P.m[2] - cpos[2];
         const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
-        sh_basis(deg, dx * il, dy * il, dz * il, Y);
+        sh_basis(DEG, dx * il, dy * il, dz * il, Y);
         float rgb[3];
-        sh_colour(sm, t, deg, Y, rgb);
+        sh_colour<DEG>(sm, t, Y, rgb);
         float ctr[4];
         precise_centre(P.m, cam, ctr);
         float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 4 * vi;
@@ -625,9 +639,10 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project(ProjLaunch p) {
 }
 
 // Half-plane terms of the gathered near-degenerate (view, splat) records, FP64.
+// Entry e goes to block e % grid, so that a short list still spreads over all SMs.
 __global__ void __launch_bounds__(kProjBlock) k_project_fp64(ProjLaunch p) {
     const uint32_t cnt = min(p.out.fp64_list[0], (uint32_t)p.n_views * (uint32_t)p.g.n);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = blockIdx.x + gridDim.x * threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
         const uint32_t vi = p.out.fp64_list[1 + e];
         const int v = (int)(vi / (uint32_t)p.g.n), i = (int)(vi - (uint32_t)v * (uint32_t)p.g.n);
         const Params P = load_params(p.g, i);
@@ -759,16 +774,21 @@ __device__ __forceinline__ Grads proj_vjp_fp64(const Params &P, const hgs_camera
     return r;
 }
 
-__global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) {
+// One thread per splat.  SH gradients are gathered in shared rows and written out
+// coalesced.  With one view (ONE_VIEW) each thread's gradient row overwrites its
+// own coefficient row once the coefficients have been read, which halves the
+// shared memory of a block; with several views the rows are separate and summed.
+template <int DEG, bool ONE_VIEW>
+__global__ void __launch_bounds__(kProjBlock, 4) k_project_bwd(ProjBwdLaunch p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem &sm = *reinterpret_cast<StageSmem *>(smem_raw);
-    float *gsh_s = reinterpret_cast<float *>(smem_raw + sizeof(StageSmem));   // [kProjBlock][stride]
+    float *gsh_s = ONE_VIEW ? sm.sh : reinterpret_cast<float *>(smem_raw + sizeof(StageSmem));
     const int n = p.g.n;
     const int base = blockIdx.x * kProjBlock;
     const int rows = min(kProjBlock, n - base);
-    const int deg = p.g.sh_degree;
-    const int nc = (deg + 1) * (deg + 1), nc3 = 3 * nc, shs = sh_stride(deg);
-    for (int j = threadIdx.x; j < kProjBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
+    constexpr int nc = (DEG + 1) * (DEG + 1), nc3 = 3 * nc, shs = DEG == 3 ? kShStride3 : nc3;
+    if (!ONE_VIEW)
+        for (int j = threadIdx.x; j < kProjBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
     stage_params(p.g, base, rows, sm);
     const int t = threadIdx.x;
     const float lp = p.cfg.lowpass;
@@ -779,6 +799,7 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) 
         const Params P = read_params(sm, t);
         float *gsh = gsh_s + t * shs;
         const float *shc = sm.sh + t * shs;
+        bool wrote = false;
         for (int v = 0; v < p.n_views; ++v) {
             const size_t vi = (size_t)v * n + i;
             const float4 *g4 = reinterpret_cast<const float4 *>(p.grad2d) + 3 * vi;
@@ -806,30 +827,54 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) 
             const float il = rsqrtf(dot3(dv, dv));
             const float dir[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
             float Y[16];
-            sh_basis(deg, dir[0], dir[1], dir[2], Y);
+            sh_basis(DEG, dir[0], dir[1], dir[2], Y);
             float raw[3];
-            sh_colour(sm, t, deg, Y, raw);
+            sh_colour<DEG>(sm, t, Y, raw);
             float graw[3];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) graw[ch] = raw[ch] < 0.0f ? 0.0f : g2.v[9 + ch];
+            // d rgb / d coefficient (l, ch) = Y_l (into the shared row), and
+            // wl[l] = sum_ch graw[ch] c[l][ch] for the direction gradient
             float wl[16];
 #pragma unroll
-            for (int l = 0; l < 16; ++l) {
-                wl[l] = 0.0f;
-                if (l < nc) {
+            for (int l = 0; l < 16; ++l) wl[l] = 0.0f;
+            wrote = true;
+            if (DEG == 3) {
+                float4 *g4s = reinterpret_cast<float4 *>(gsh);
+                const float4 *c4 = reinterpret_cast<const float4 *>(shc);
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    const float4 c = c4[q];                     // read before an in-place overwrite
+                    float4 a = ONE_VIEW ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : g4s[q];
+                    a.x += graw[(4 * q) % 3] * Y[(4 * q) / 3];
+                    a.y += graw[(4 * q + 1) % 3] * Y[(4 * q + 1) / 3];
+                    a.z += graw[(4 * q + 2) % 3] * Y[(4 * q + 2) / 3];
+                    a.w += graw[(4 * q + 3) % 3] * Y[(4 * q + 3) / 3];
+                    g4s[q] = a;
+                    wl[(4 * q) / 3] += graw[(4 * q) % 3] * c.x;
+                    wl[(4 * q + 1) / 3] += graw[(4 * q + 1) % 3] * c.y;
+                    wl[(4 * q + 2) / 3] += graw[(4 * q + 2) % 3] * c.z;
+                    wl[(4 * q + 3) / 3] += graw[(4 * q + 3) % 3] * c.w;
+                }
+            } else {
+#pragma unroll
+                for (int l = 0; l < nc; ++l) {
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
-                        gsh[3 * l + ch] += graw[ch] * Y[l];
-                        wl[l] += graw[ch] * shc[3 * l + ch];
+                        const float c = shc[3 * l + ch];
+                        wl[l] += graw[ch] * c;
+                        gsh[3 * l + ch] = (ONE_VIEW ? 0.0f : gsh[3 * l + ch]) + graw[ch] * Y[l];
                     }
                 }
             }
             float gd[3];
-            sh_grad_dot(deg, dir[0], dir[1], dir[2], wl, gd);
+            sh_grad_dot(DEG, dir[0], dir[1], dir[2], wl, gd);
             const float dd = dot3(gd, dir);
 #pragma unroll
             for (int k = 0; k < 3; ++k) gm[k] += (gd[k] - dd * dir[k]) * il;
         }
+        if (ONE_VIEW && !wrote)
+            for (int j = 0; j < nc3; ++j) gsh[j] = 0.0f;
         const bool acc = p.cfg.accumulate != 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -862,7 +907,7 @@ __global__ void __launch_bounds__(kProjBlock, 3) k_project_bwd(ProjBwdLaunch p) 
 // since one splat can be listed for several views.
 __global__ void __launch_bounds__(kProjBlock) k_project_bwd_fp64(ProjBwdLaunch p) {
     const uint32_t cnt = min(p.fp64_list[0], (uint32_t)p.n_views * (uint32_t)p.g.n);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = blockIdx.x + gridDim.x * threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
         const uint32_t vi = p.fp64_list[1 + e];
         const int v = (int)(vi / (uint32_t)p.g.n), i = (int)(vi - (uint32_t)v * (uint32_t)p.g.n);
         const Params P = load_params(p.g, i);
@@ -887,34 +932,64 @@ __global__ void __launch_bounds__(kProjBlock) k_project_bwd_fp64(ProjBwdLaunch p
 
 }  // namespace
 
-size_t project_smem_bytes(bool bwd) {
-    return sizeof(StageSmem) + (bwd ? sizeof(float) * kShStride3 * kProjBlock : 0);
+size_t project_smem_bytes(bool separate_sh_grads) {
+    return sizeof(StageSmem) + (separate_sh_grads ? sizeof(float) * kShStride3 * kProjBlock : 0);
 }
 
 // Grid of the FP64 follow-up kernels: the list length is known only on the device,
 // so a fixed grid strides over it (one thread per entry while it is short).
 constexpr int kFp64Blocks = 148;
 
+template <int DEG>
+cudaError_t launch_project_deg(const ProjLaunch &p, cudaStream_t s) {
+    const size_t smem = project_smem_bytes(false);
+    cudaError_t e = cudaFuncSetAttribute(k_project<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_project<DEG><<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int DEG, bool ONE_VIEW>
+cudaError_t launch_project_bwd_deg(const ProjBwdLaunch &p, cudaStream_t s) {
+    const size_t smem = project_smem_bytes(!ONE_VIEW);
+    cudaError_t e = cudaFuncSetAttribute(k_project_bwd<DEG, ONE_VIEW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_project_bwd<DEG, ONE_VIEW><<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int DEG>
+cudaError_t launch_project_bwd_views(const ProjBwdLaunch &p, cudaStream_t s) {
+    return p.n_views == 1 ? launch_project_bwd_deg<DEG, true>(p, s) : launch_project_bwd_deg<DEG, false>(p, s);
+}
+
 cudaError_t launch_project(const ProjLaunch &p, cudaStream_t s) {
     if (p.g.n == 0) return cudaSuccess;
-    const size_t smem = project_smem_bytes(false);
-    cudaError_t e = cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaMemsetAsync(p.out.fp64_list, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(p.out.fp64_list, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_project<<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (p.g.sh_degree) {
+        case 0: e = launch_project_deg<0>(p, s); break;
+        case 1: e = launch_project_deg<1>(p, s); break;
+        case 2: e = launch_project_deg<2>(p, s); break;
+        default: e = launch_project_deg<3>(p, s); break;
+    }
+    if (e != cudaSuccess) return e;
     k_project_fp64<<<kFp64Blocks, kProjBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project_bwd(const ProjBwdLaunch &p, cudaStream_t s) {
     if (p.g.n == 0) return cudaSuccess;
-    const size_t smem = project_smem_bytes(true);
-    cudaError_t e = cudaFuncSetAttribute(k_project_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaMemsetAsync(p.fp64_list, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(p.fp64_list, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_project_bwd<<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (p.g.sh_degree) {
+        case 0: e = launch_project_bwd_views<0>(p, s); break;
+        case 1: e = launch_project_bwd_views<1>(p, s); break;
+        case 2: e = launch_project_bwd_views<2>(p, s); break;
+        default: e = launch_project_bwd_views<3>(p, s); break;
+    }
+    if (e != cudaSuccess) return e;
     k_project_bwd_fp64<<<kFp64Blocks, kProjBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
