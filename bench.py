@@ -306,10 +306,10 @@ def alg_bytes(n, n_pairs, total_tiles):
 #   full   : Eq. 8 via A&S 7.1.26, Eq. 10 mix, clamp, floor compare     20 FP32 + 3 MUFU
 #   comp   : transmittance update, stop test, colour accumulation       7 FP32
 #   contrib: backward adjoint of one composited pair                   58 FP32 + 2 MUFU
-#   red    : warp reduction of 12 gradients (5 shuffle+add levels,
-#            all 32 lanes)                                            1920 FP32
+#   red    : fold of 12 gradients over lane pairs (one shuffle+add
+#            level, all 32 lanes) when more than 16 lanes contribute    384 FP32
 OPS = {"fwd": {"fp32": {"fwd_visit": 9, "fwd_full": 20, "fwd_comp": 7}, "mufu": {"fwd_full": 3}},
-       "bwd": {"fp32": {"bwd_visit": 9, "bwd_full": 20, "bwd_contrib": 58, "bwd_warp_red": 1920},
+       "bwd": {"fp32": {"bwd_visit": 9, "bwd_full": 20, "bwd_contrib": 58, "bwd_warp_red": 384},
                "mufu": {"bwd_full": 3, "bwd_contrib": 2}}}
 
 
