@@ -58,7 +58,7 @@ Ws carve(void *base, size_t vn, size_t cap, size_t *total) {
     Ws w{};
     w.depth_parts = std::max<size_t>((vn + kPart - 1) / kPart, 1);
     w.pair_parts = std::max<size_t>((cap + kPart - 1) / kPart, 1);
-    w.parts_stride = std::max(w.depth_parts, w.pair_parts);
+    w.parts_stride = (std::max(w.depth_parts, w.pair_parts) + 3) & ~(size_t)3;   // rows 16-B aligned
     size_t off = 0;
     char *b = static_cast<char *>(base);
     auto take = [&](size_t bytes) { char *p = b ? b + off : nullptr; off += align_up(bytes); return p; };
@@ -116,6 +116,9 @@ __global__ void __launch_bounds__(kBlock) k_depth_keys(const uint32_t *__restric
 }
 
 // ---- radix pass, part 1: digit counts of every partition ---------------------------------
+// Each thread counts 16 consecutive keys, fetched with four 128-bit loads that are
+// all in flight at once (the counts of a partition do not depend on the order in
+// which its keys are visited).
 __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__ keys, Count cnt, int shift,
                                                     uint32_t *__restrict__ counts, size_t stride) {
     __shared__ uint32_t s_cnt[kBlock / 32][kRadix];
@@ -125,12 +128,22 @@ __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__
     for (uint32_t part = blockIdx.x; part < n_parts; part += gridDim.x) {
         for (int j = lane; j < kRadix; j += 32) s_cnt[warp][j] = 0;
         __syncwarp();
-        const uint32_t wbase = part * kPart + warp * (32 * kItems);
-#pragma unroll 4
-        for (int it = 0; it < kItems; ++it) {
-            const uint32_t idx = wbase + it * 32 + lane;
-            if (idx < K) atomicAdd(&s_cnt[warp][(keys[idx] >> shift) & (kRadix - 1)], 1u);
+        const uint32_t base = part * kPart + tid * kItems;
+        uint32_t k[kItems];
+        if (base + kItems <= K) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(keys + base);
+#pragma unroll
+            for (int q = 0; q < kItems / 4; ++q) {
+                const uint4 t = src[q];
+                k[4 * q] = t.x; k[4 * q + 1] = t.y; k[4 * q + 2] = t.z; k[4 * q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) k[j] = base + j < K ? keys[base + j] : 0u;
         }
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+            if (base + j < K) atomicAdd(&s_cnt[warp][(k[j] >> shift) & (kRadix - 1)], 1u);
         __syncthreads();
         uint32_t total = 0;
 #pragma unroll
@@ -141,29 +154,60 @@ __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__
 }
 
 // ---- radix pass, part 2: per digit, exclusive scan of the counts over partitions ---------
-// One warp per digit; the digit totals go to ctrl->totals.
+// One block per digit, 16 consecutive counts per thread (4096 partitions per round,
+// so one round below 16.7M elements); the digit totals go to ctrl->totals.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp);
+
 __global__ void __launch_bounds__(kBlock) k_digit_scan(uint32_t *__restrict__ counts, Count cnt, size_t stride,
                                                        Ctrl *ctrl) {
-    const int d = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
-    const int lane = lane_id();
-    if (d >= kRadix) return;
+    __shared__ uint32_t s_tmp[kBlock / 32];
+    __shared__ uint32_t s_total;
+    const int d = blockIdx.x;
     const uint32_t K = cnt.get();
     const uint32_t n_parts = (K + kPart - 1) / kPart;
     uint32_t *row = counts + (size_t)d * stride;
-    uint32_t run = 0;
-    for (uint32_t base = 0; base < n_parts; base += 32) {
-        const uint32_t j = base + lane;
-        const uint32_t v = j < n_parts ? row[j] : 0u;
-        uint32_t x = v;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n_parts; base += kPart) {
+        const uint32_t j0 = base + threadIdx.x * kItems;
+        const bool full = j0 + kItems <= n_parts;
+        uint32_t v[kItems];
+        if (full) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(row + j0);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            for (int q = 0; q < kItems / 4; ++q) {
+                const uint4 t = src[q];
+                v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) v[j] = j0 + j < n_parts ? row[j0 + j] : 0u;
         }
-        if (j < n_parts) row[j] = run + x - v;
-        run += __shfl_sync(0xffffffffu, x, 31);
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) sum += v[j];
+        const uint32_t excl = block_excl_scan(sum, s_tmp);
+        uint32_t run = carry + excl;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const uint32_t c = v[j];
+            v[j] = run;
+            run += c;
+        }
+        if (full) {
+            uint4 *dst = reinterpret_cast<uint4 *>(row + j0);
+#pragma unroll
+            for (int q = 0; q < kItems / 4; ++q) dst[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kItems; ++j)
+                if (j0 + j < n_parts) row[j0 + j] = v[j];
+        }
+        if (threadIdx.x == kBlock - 1) s_total = excl + sum;
+        __syncthreads();
+        carry += s_total;
+        __syncthreads();
     }
-    if (lane == 0) ctrl->totals[d] = run;
+    if (threadIdx.x == 0) ctrl->totals[d] = carry;
 }
 
 // ---- radix pass, part 3: rank and scatter ------------------------------------------------
@@ -441,14 +485,40 @@ __global__ void __launch_bounds__(kBlock) k_duplicate(DupArgs a) {
 }
 
 // ---- A5: tile ranges from the sorted 32-bit tile keys ------------------------------------
+// Each thread reads 4 consecutive keys with one 128-bit load; the neighbours across
+// threads come by shuffle (two extra loads per warp at its ends).  A start (end) of
+// tile t is where the previous (next) key differs; 0xFFFFFFFF past both ends.
 __global__ void __launch_bounds__(kBlock) k_ranges(const uint32_t *__restrict__ tk, Count cnt, int total_tiles,
                                                    uint32_t *ranges, int *status) {
     const size_t K = cnt.get();
-    for (size_t i = (size_t)blockIdx.x * kBlock + threadIdx.x; i < K; i += (size_t)gridDim.x * kBlock) {
-        const uint32_t t = tk[i];
-        if (t >= (uint32_t)total_tiles) { set_status(status, HGS_DEV_BOUNDS); continue; }
-        if (i == 0 || tk[i - 1] != t) ranges[2 * (size_t)t] = (uint32_t)i;
-        if (i == K - 1 || tk[i + 1] != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
+    const size_t n4 = (K + 3) / 4;
+    const int lane = lane_id();
+    constexpr uint32_t kNone = 0xffffffffu;
+    for (size_t g = (size_t)blockIdx.x * kBlock + threadIdx.x; g - lane < n4; g += (size_t)gridDim.x * kBlock) {
+        const size_t i0 = 4 * g;
+        uint32_t k[4];
+        if (i0 + 4 <= K) {
+            const uint4 t = *reinterpret_cast<const uint4 *>(tk + i0);
+            k[0] = t.x; k[1] = t.y; k[2] = t.z; k[3] = t.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[j] = i0 + j < K ? tk[i0 + j] : kNone;
+        }
+        uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+        if (lane == 0) prev = (i0 > 0 && i0 - 1 < K) ? tk[i0 - 1] : kNone;
+        if (lane == 31) next = i0 + 4 < K ? tk[i0 + 4] : kNone;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const size_t i = i0 + j;
+            if (i >= K) break;
+            const uint32_t t = k[j];
+            if (t >= (uint32_t)total_tiles) { set_status(status, HGS_DEV_BOUNDS); continue; }
+            const uint32_t p = j ? k[j - 1] : prev;
+            const uint32_t nx = j < 3 ? k[j + 1] : next;
+            if (p != t) ranges[2 * (size_t)t] = (uint32_t)i;
+            if (nx != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
+        }
     }
 }
 
@@ -472,7 +542,7 @@ cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
                        cudaStream_t s) {
     const int parts = (int)std::max<size_t>((max_elems + kPart - 1) / kPart, 1);
     k_upsweep<<<std::min(parts, g_aux_blocks), kBlock, 0, s>>>(kin, cnt, shift, w.counts, w.parts_stride);
-    k_digit_scan<<<kRadix / (kBlock / 32), kBlock, 0, s>>>(w.counts, cnt, w.parts_stride, w.ctrl);
+    k_digit_scan<<<kRadix, kBlock, 0, s>>>(w.counts, cnt, w.parts_stride, w.ctrl);
     DownArgs a{};
     a.kin = kin;
     a.vin = vin;
