@@ -274,12 +274,12 @@ def n_sort_passes(total_tiles):
 
 
 def launches_per_step(total_tiles, persistent=False):
-    """Kernels of one fwd+bwd step: k_project; binning = k_depth_keys, 3 per radix
-    pass (k_upsweep, k_digit_scan, k_downsweep), k_scan, k_duplicate, k_ranges;
-    k_render_fwd (+ k_queue_count, k_queue_fill when persistent); k_render_bwd;
-    k_project_bwd."""
+    """Kernels of one fwd+bwd step: k_project + k_project_fp64; binning =
+    k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep), k_scan,
+    k_duplicate, k_ranges; k_render_fwd (+ k_queue_count, k_queue_fill when
+    persistent); k_render_bwd; k_project_bwd + k_project_bwd_fp64."""
     dp, tp = n_sort_passes(total_tiles)
-    return 1 + (1 + 3 * dp + 2 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 1
+    return 2 + (1 + 3 * dp + 2 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 2
 
 
 def alg_bytes(n, n_pairs, total_tiles):
