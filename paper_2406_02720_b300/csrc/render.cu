@@ -95,7 +95,7 @@ struct Batch {
 // cut-off test of eval_alpha is culled.
 template <int BATCH>
 __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH> &s, int k,
-                                      float ox, float oy) {
+                                      float ox, float oy, bool plain) {
     const float4 r0 = __ldg(rec + 4 * (size_t)id);
     const float4 r1 = __ldg(rec + 4 * (size_t)id + 1);
     const float4 r2 = __ldg(rec + 4 * (size_t)id + 2);
@@ -103,7 +103,7 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     const float mx = __fadd_rn(__fsub_rn(r0.x, ox), r0.z);
     const float my = __fadd_rn(__fsub_rn(r0.y, oy), r0.w);
     const float u11 = __fmul_rn(kUScale, r1.x), u12 = __fmul_rn(kUScale, r1.y), u22 = __fmul_rn(kUScale, r1.z);
-    const float a1 = r2.y, a2 = r2.z;
+    const float a1 = r2.y, a2 = plain ? r2.y : r2.z;     // plain 3D-GS: alpha = alpha1 G
     const float amax = fmaxf(a1, a2);
     // alpha <= amax * G < 1/255 whenever log2 G < -log2(255 amax); 1e-3 covers ex2/lg2 error
     const float qcut = amax > 0.0f ? __fadd_rn(lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : -1.0f;
@@ -252,6 +252,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
     const float cxb = (float)(bx - ox) + 4.0f, cyb = (float)(by - oy) + 2.0f;   // block centre
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
+    const bool plain = p.cfg.plain != 0;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0;
     bool done = !inside;
@@ -263,7 +264,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
             if (j < ti.end) {
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH>(rec, id, s, k, fox, foy);
+                stage<BATCH>(rec, id, s, k, fox, foy, plain);
             }
         }
         __syncthreads();
@@ -314,6 +315,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
 }
 
 // ---- backward ------------------------------------------------------------------------
+
 // A splat's 12 gradients from the lanes of a warp go to global memory as float4
 // atomic adds (3 per lane).  When more than 16 lanes contribute, one xor-shuffle
 // level first folds lane l + 16 into lane l, so at most 16 lanes issue atomics:
@@ -327,7 +329,7 @@ __device__ __forceinline__ void atomic_add12(float *dst, const float g[12]) {
     atomicAdd(d4 + 2, make_float4(g[8], g[9], g[10], g[11]));
 }
 
-template <int TW, int TH, int BATCH, bool COUNT>
+template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
 __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s,
                                                 uint32_t &s_maxlast) {
     constexpr int NT = TW * TH;
@@ -362,6 +364,8 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
     __syncthreads();
     const uint32_t tile_end = min(ti.end, ti.beg + s_maxlast);
     const float bgg = ti.bg[0] * g0_ + ti.bg[1] * g1_ + ti.bg[2] * g2_;
+    const float TfB = Tf * bgg;             // d L / d a_i gets -T_final bg.g / (1 - a_i)
+    constexpr bool plain = PLAIN;
     float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
     float *grad = p.grad2d;
     unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0;
@@ -373,7 +377,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
             if (j < bend) {
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH>(rec, id, s, k, fox, foy);
+                stage<BATCH>(rec, id, s, k, fox, foy, plain);
             }
         }
         __syncthreads();
@@ -402,19 +406,24 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                     const float4 g2 = s.g2[k];
                     const float cb = s.b[k];
                     const float one_m_a = __fsub_rn(1.0f, ev.a);
-                    const float Ti = __fdividef(T, one_m_a);
+                    const float rinv = __fdividef(1.0f, one_m_a);
+                    const float Ti = T * rinv;
                     const float w = ev.a * Ti;
                     gr[9] = w * g0_; gr[10] = w * g1_; gr[11] = w * g2_;
                     float dLda = Ti * ((g2.z - S0) * g0_ + (g2.w - S1) * g1_ + (cb - S2) * g2_);
-                    dLda -= __fdividef(Tf * bgg, one_m_a);
+                    dLda -= TfB * rinv;
                     S0 = ev.a * g2.z + one_m_a * S0;
                     S1 = ev.a * g2.w + one_m_a * S1;
                     S2 = ev.a * cb + one_m_a * S2;
                     T = Ti;
                     if (!ev.clamped) {
                         const float dA = dLda * ev.G;
-                        gr[7] = dA * ev.P;
-                        gr[8] = dA - gr[7];
+                        if (plain) {
+                            gr[7] = dA;                  // alpha = alpha1 G: nothing to alpha2 or w'
+                        } else {
+                            gr[7] = dA * ev.P;
+                            gr[8] = dA - gr[7];
+                        }
                         const float dpow = dLda * ev.A * ev.G;
                         const float dx = ev.dx, dy = ev.dy;
                         gr[2] = -0.5f * dpow * dx * dx;
@@ -424,7 +433,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                         const float sc = dpow * kInvUScale2;
                         gr[0] = sc * (g0.z * ev.s1);
                         gr[1] = sc * (g0.w * ev.s1 + g1.x * ev.s2);
-                        if (fabsf(g1.z) + fabsf(g1.w) < kStepDetect) {
+                        if (!plain && fabsf(g1.z) + fabsf(g1.w) < kStepDetect) {
                             const float dz = dA * g2.y * ev.e * kInvSqrtPi;
                             gr[5] = dz * dx;
                             gr[6] = dz * dy;
@@ -485,12 +494,12 @@ __global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 5>)) k_render_fwd
     }
 }
 
-template <int TW, int TH, int BATCH, bool COUNT>
+template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
 __global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 4>)) k_render_bwd(RenderLaunch p) {
     __shared__ Batch<BATCH> s;
     __shared__ uint32_t s_maxlast;
     if (!p.cfg.persistent) {
-        render_tile_bwd<TW, TH, BATCH, COUNT>(p, blockIdx.x, s, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, blockIdx.x, s, s_maxlast);
         return;
     }
     Queue *q = reinterpret_cast<Queue *>(p.ws);
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 4>)) k_render_bwd
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= (uint32_t)p.vt.total_tiles) break;
-        render_tile_bwd<TW, TH, BATCH, COUNT>(p, (int)order[item], s, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, (int)order[item], s, s_maxlast);
         __syncthreads();
     }
 }
@@ -538,9 +547,9 @@ __global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, 
     }
 }
 
-template <int TW, int TH, int BATCH, bool FWD, bool COUNT>
+template <int TW, int TH, int BATCH, bool FWD, bool COUNT, bool PLAIN>
 cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
-    auto kern = FWD ? k_render_fwd<TW, TH, BATCH, COUNT> : k_render_bwd<TW, TH, BATCH, COUNT>;
+    auto kern = FWD ? k_render_fwd<TW, TH, BATCH, COUNT> : k_render_bwd<TW, TH, BATCH, COUNT, PLAIN>;
     if (!p.cfg.persistent) {
         kern<<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
         return cudaGetLastError();
@@ -555,9 +564,14 @@ cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The forward handles plain 3D-GS while staging (alpha2 := alpha1); the backward
+// kernel is specialised on it, so the default path carries no test of the flag.
 template <int TW, int TH, int BATCH, bool FWD>
 cudaError_t launch_c(const RenderLaunch &p, cudaStream_t s) {
-    return p.counters ? launch_t<TW, TH, BATCH, FWD, true>(p, s) : launch_t<TW, TH, BATCH, FWD, false>(p, s);
+    const bool plain = !FWD && p.cfg.plain;
+    if (p.counters)
+        return plain ? launch_t<TW, TH, BATCH, FWD, true, true>(p, s) : launch_t<TW, TH, BATCH, FWD, true, false>(p, s);
+    return plain ? launch_t<TW, TH, BATCH, FWD, false, true>(p, s) : launch_t<TW, TH, BATCH, FWD, false, false>(p, s);
 }
 
 cudaError_t prepare_queue(const RenderLaunch &p, cudaStream_t s) {

@@ -95,6 +95,26 @@ def test_equal_opacity_is_bitwise_plain_3dgs(cuda_ok):
     assert np.all(ga["normals"] == 0.0)
 
 
+def test_plain_mode_against_oracle(cuda_ok):
+    """hgs_config.plain = 1 renders plain 3D-GS (alpha = alpha1 G) from the same records:
+    image and gradients against the oracle's plain mode, on a scene whose half opacities
+    differ (so the flag visibly changes the image)."""
+    rng = np.random.default_rng(37)
+    sc = scenes.scene_uniform(rng, 800, [-1.3, -0.8, 2.5], [1.3, 0.8, 6], -3.3, 0.5, 1.5, 3)
+    cams = [scenes.identity_camera(160, 96, 90.0, 80.0, 48.0, bg=(0.3, 0.2, 0.1))]
+    ref = oracle.render(sc, cams[0], plain=True)
+    half = oracle.render(sc, cams[0])
+    assert np.abs(half["image"] - ref["image"]).max() > 1e-2
+    dL = masked_upstream(scenes.upstream_grad(103, cams), [ref])
+    out = gpu_render(sc, cams, plain=True, dL=dL)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    gref = oracle.render_bwd(sc, cams[0], dL[0], plain=True, proj=ref["proj"], bins=ref["bins"])
+    assert np.all(out["grads"]["opac2"] == 0.0) and np.all(out["grads"]["normals"] == 0.0)
+    for k in ("means", "scales", "quats", "opac1", "sh"):
+        bad, _ = grad_close(out["grads"][k], gref[k])
+        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
+
+
 def test_complement_symmetry(cuda_ok):
     sc, cams = _ragged_scene(seed=6)
     b = scenes.Scene(sc.means, sc.scales, sc.quats, -sc.normals, sc.opac2.copy(), sc.opac1.copy(), sc.sh,
