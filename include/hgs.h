@@ -99,8 +99,9 @@ typedef struct {
 /* Options.
  *   tile_w, tile_h : 8x8, 16x16 or 32x8.  The tile shape changes the image
  *                    (tiles are culled by the 3-sigma square, not per pixel).
- *   batch          : splats staged in shared memory per round, 32..256,
- *                    multiple of 32 (0 = tile_w*tile_h)
+ *   batch          : splats staged in shared memory per round: 32, 64, 128,
+ *                    256 or 512 (0 = tile_w*tile_h forward and twice that,
+ *                    at most 512, backward)
  *   lowpass        : l added to the diagonal of hat Sigma (3D-GS uses 0.3)
  *   fov_clamp      : 1 = clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS)
  *   plain          : 1 = plain 3D-GS weight alpha1 * hat G (no half split)
