@@ -64,6 +64,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float lg2_approx(float x) {
     float y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -114,24 +120,37 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     s.id[k] = id;
     float4 cu = make_float4(-1.0f, -1.0f, 0.0f, 0.0f);
     if (qcut >= 0.0f) {
-        const float rq = sqrtf(qcut);
+        // Approximate reciprocals and roots (a few ulp) are enough here: every bound
+        // is inflated by 1.001 and 1e-3 px, far beyond their error.
+        const float rq = sqrt_approx(qcut);
+        const float i11 = rcp_approx(u11), i22 = rcp_approx(u22);
         // axis-aligned half-extents: h(e_x) = rq |U^-T e_x|, h(e_y) = rq / u22
-        const float ru = u12 / u22;
-        const float hx = rq * sqrtf(1.0f + ru * ru) / u11;
-        const float hy = rq / u22;
+        const float ru = u12 * i22;
+        const float hx = rq * sqrt_approx(1.0f + ru * ru) * i11;
+        const float hy = rq * i22;
         // minor axis: eigenvector of Q = U^T U for its larger eigenvalue
         const float A = u11 * u11, B = u11 * u12, C = u12 * u12 + u22 * u22;
-        const float lmax = 0.5f * (A + C) + sqrtf(0.25f * (A - C) * (A - C) + B * B);
+        const float lmax = 0.5f * (A + C) + sqrt_approx(0.25f * (A - C) * (A - C) + B * B);
         float nx = A >= C ? lmax - C : B;
         float ny = A >= C ? B : lmax - A;
-        const float nl = sqrtf(nx * nx + ny * ny);
-        if (nl > 0.0f && nl < 1e30f) { nx /= nl; ny /= nl; } else { nx = 1.0f; ny = 0.0f; }
-        // h(n) = rq |z|, U^T z = n
-        const float z1 = nx / u11;
-        const float z2 = (ny - u12 * z1) / u22;
-        const float hn = rq * sqrtf(z1 * z1 + z2 * z2);
+        const float nl2 = nx * nx + ny * ny;
+        if (nl2 > 0.0f && nl2 < 1e30f) {
+            const float il = rsqrtf(nl2);
+            nx *= il;
+            ny *= il;
+        } else {
+            nx = 1.0f;
+            ny = 0.0f;
+        }
+        // h(n) = rq |z| with U^T z = n, for the (nearly) unit n actually stored: the
+        // test below uses h of the stored direction, so it stays exact whatever the
+        // rounding of n
+        const float z1 = nx * i11;
+        const float z2 = (ny - u12 * z1) * i22;
+        const float hn = rq * sqrt_approx(z1 * z1 + z2 * z2);
         const float tn = hn * 1.001f + 1e-3f + (fabsf(nx) * 3.5f + fabsf(ny) * 1.5f) * 1.0001f;
-        cu = make_float4(hx * 1.001f + 1e-3f + 3.5f, hy * 1.001f + 1e-3f + 1.5f, nx / tn, ny / tn);
+        const float itn = rcp_approx(tn);
+        cu = make_float4(hx * 1.001f + 1e-3f + 3.5f, hy * 1.001f + 1e-3f + 1.5f, nx * itn, ny * itn);
     }
     s.cu[k] = cu;
 }
