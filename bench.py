@@ -276,11 +276,11 @@ def n_sort_passes(total_tiles):
 
 def launches_per_step(total_tiles, persistent=False):
     """Kernels of one fwd+bwd step: k_project + k_project_fp64; binning =
-    k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep), k_scan,
-    k_duplicate, k_ranges; k_render_fwd (+ k_queue_count, k_queue_fill when
-    persistent); k_render_bwd; k_project_bwd + k_project_bwd_fp64."""
+    k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep),
+    k_scan_reduce, k_chunk_scan, k_duplicate, k_ranges; k_render_fwd (+ k_queue_count,
+    k_queue_fill when persistent); k_render_bwd; k_project_bwd + k_project_bwd_fp64."""
     dp, tp = n_sort_passes(total_tiles)
-    return 2 + (1 + 3 * dp + 2 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 2
+    return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 2
 
 
 def alg_bytes(n, n_pairs, total_tiles):
@@ -290,7 +290,8 @@ def alg_bytes(n, n_pairs, total_tiles):
                     tiles 4) per splat
       bin         : per splat: depth keys 16 (read depth+tiles, write key+id), 4 depth
                     passes x 20 (upsweep reads 4, downsweep reads 8 writes 8), scan 12
-                    (order, tiles, offset), duplicate 24 (order, offset, rect);
+                    (read order + tiles, write tiles in depth order), duplicate 24
+                    (order, tiles in depth order, rect);
                     per pair: 8 written by duplicate, 20 per tile pass, 4 read by ranges;
                     8 per tile written by ranges
       project_bwd : 252 B parameters + 48 B screen-space gradients read, 252 B written

@@ -58,7 +58,8 @@ typedef enum {
 
 /* bits OR-ed into *dev_status by kernels */
 #define HGS_DEV_CAPACITY 0x1  /* more (tile, splat) pairs than pair_capacity     */
-#define HGS_DEV_TIMEOUT 0x2   /* a look-back or queue spin hit its iteration cap */
+#define HGS_DEV_TIMEOUT 0x2   /* reserved: no kernel of this version waits on
+                                 another block or warp, so none can time out    */
 #define HGS_DEV_BOUNDS 0x4    /* an index was outside its array; access skipped  */
 
 /* Half-Gaussian parameters (Sec. 3.2), activated values, [n] rows:

@@ -32,30 +32,8 @@ __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int gtile) {
 
 __host__ __device__ __forceinline__ int div_up(int a, int b) { return (a + b - 1) / b; }
 
-// Bounded spin-waits: the cap, and how long a waiting thread backs off.
-constexpr unsigned kSpinCap = 1u << 22;
-constexpr unsigned kSpinSleepNs = 64;
-
 __device__ __forceinline__ void set_status(int *st, int bit) {
     if (st) atomicOr(st, bit);
-}
-
-// Relaxed device-scope 32/64-bit load and store (look-back words; L1 bypassed).
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Host-side launchers (one per kernel family), defined in the .cu files.
