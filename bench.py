@@ -141,7 +141,7 @@ def run_gpu(args):
     sc, cams, dL_np = _scene(args)
     W, H_ = cams[0].width, cams[0].height
     pixels = W * H_ * len(cams)
-    cfg = H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch)
+    cfg = H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch, persistent=args.persistent)
     g = Gaussians.from_scene(sc, dev)
     rast = Rasterizer(cams, sc.n, cfg, device=dev)
     rast.forward(g)                                     # sizes the pair buffers
@@ -240,7 +240,9 @@ def run_gpu(args):
         "data": "synthetic (seeded scene shaped like the paper's: 3M kernels in blobs, bimodal half opacities)",
         "config": {"workload": f"config3: {sc.n} half-Gaussians, SH degree 3, {W}x{H_}, 1 view, fwd+bwd, CUDA graph",
                    "n_splats": sc.n, "width": W, "height": H_, "views": len(cams),
-                   "tile": f"{args.tile_w}x{args.tile_h}", "batch": args.batch or f"{args.tile_w * args.tile_h} fwd / {min(2 * args.tile_w * args.tile_h, 512)} bwd",
+                   "tile": f"{args.tile_w}x{args.tile_h}",
+                   "compositing": "persistent heaviest-first queue" if args.persistent else "one block per tile",
+                   "batch": args.batch or f"{args.tile_w * args.tile_h} fwd / {min(2 * args.tile_w * args.tile_h, 512)} bwd",
                    "pairs": n_pairs, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
         "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
@@ -277,10 +279,11 @@ def n_sort_passes(total_tiles):
 def launches_per_step(total_tiles, persistent=False):
     """Kernels of one fwd+bwd step: k_project + k_project_fp64; binning =
     k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep),
-    k_scan_reduce, k_chunk_scan, k_duplicate, k_ranges; k_render_fwd (+ k_queue_count,
-    k_queue_fill when persistent); k_render_bwd; k_project_bwd + k_project_bwd_fp64."""
+    k_scan_reduce, k_chunk_scan, k_duplicate, k_ranges; k_render_fwd and k_render_bwd,
+    each after k_queue_count + k_queue_fill when persistent; k_project_bwd +
+    k_project_bwd_fp64."""
     dp, tp = n_sort_passes(total_tiles)
-    return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 2
+    return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + 2 * (3 if persistent else 1) + 2
 
 
 def alg_bytes(n, n_pairs, total_tiles):
@@ -531,7 +534,8 @@ def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_00
         sc, cams = scenes.config5(n=n, equal_opacity=equal)
         dL = torch.from_numpy(scenes.upstream_grad(105, cams)[0].reshape(-1)).to(dev)
         g = Gaussians.from_scene(sc, dev)
-        r = Rasterizer(cams, n, H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch), device=dev)
+        r = Rasterizer(cams, n, H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch,
+                                              persistent=args.persistent), device=dev)
         r.forward(g)
         r._alloc_pairs(int(r.num_pairs.item() * 1.05) + 4096)
         grads = Gaussians.empty_like(g)
@@ -655,6 +659,9 @@ def main(argv=None):
     ap.add_argument("--tile-w", type=int, default=16)
     ap.add_argument("--tile-h", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--per-tile", dest="persistent", action="store_false",
+                    help="one compositing block per tile instead of persistent blocks over the "
+                         "heaviest-first tile queue")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-multiview", dest="multiview", action="store_false")
     ap.add_argument("--mv-views", type=int, default=64)

@@ -4,8 +4,9 @@ launch sequence per view.
 BatchedStep: hgs_project over all views, one hgs_bin over global (view, tile)
 ids, and persistent compositing kernels that pop (view, tile) items from a
 heaviest-first queue; the projection adjoint sums over views.  PerViewStep: the
-same path run once per view (n_views = 1), the projection adjoint adding into
-the same gradient buffers (hgs_config.accumulate).  Both capture their whole
+same path run once per view (n_views = 1, each view with its own persistent tile
+queue), the projection adjoint adding into the same gradient buffers
+(hgs_config.accumulate).  Both capture their whole
 forward+backward step in one CUDA graph, so neither pays per-launch host cost.
 """
 from __future__ import annotations
@@ -52,7 +53,7 @@ class PerViewStep:
         self.rasts = []
         self.dLs = []
         for k, cam in enumerate(cams):
-            cfg = H.make_config(tile=tile, batch=batch, persistent=False, accumulate=k > 0)
+            cfg = H.make_config(tile=tile, batch=batch, persistent=True, accumulate=k > 0)
             r = Rasterizer([cam], g.n, cfg, device=device)
             r.forward(g)
             r._alloc_pairs(int(r.num_pairs.item() * 1.05) + 4096)

@@ -25,7 +25,7 @@ IMAGE_ATOL = 1e-4
 EXEMPT_ATOL = 2e-2
 
 
-def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persistent=False,
+def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persistent=True,
                pair_capacity=None, dL=None):
     import torch
     from paper_2406_02720_b300 import hgs as H
