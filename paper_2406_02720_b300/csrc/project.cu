@@ -439,8 +439,13 @@ struct StageSmem {
     float sh[kShStride3 * kProjBlock];
 };
 
-__device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, int rows, StageSmem &sm) {
+// Copies the block's parameter rows into shared memory, plus optionally `extra_floats`
+// floats per row from `extra` into `extra_dst` in the same batch of asynchronous copies.
+__device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, int rows, StageSmem &sm,
+                                             const float *extra = nullptr, int extra_floats = 0,
+                                             float *extra_dst = nullptr) {
     const int deg = g.sh_degree, nc3 = 3 * (deg + 1) * (deg + 1);
+    if (extra) stage_rows(extra + (size_t)extra_floats * base, rows, extra_floats, extra_dst, extra_floats);
     stage_rows(g.means + 3 * (size_t)base, rows, 3, sm.mean, 3);
     stage_rows(g.scales + 3 * (size_t)base, rows, 3, sm.scale, 3);
     stage_rows(g.normals + 3 * (size_t)base, rows, 3, sm.nrm, 3);
@@ -782,14 +787,20 @@ template <int DEG, bool ONE_VIEW>
 __global__ void __launch_bounds__(kProjBlock, 4) k_project_bwd(ProjBwdLaunch p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem &sm = *reinterpret_cast<StageSmem *>(smem_raw);
-    float *gsh_s = ONE_VIEW ? sm.sh : reinterpret_cast<float *>(smem_raw + sizeof(StageSmem));
+    // one view: screen-space gradient rows staged with the parameters; several views:
+    // separate SH gradient rows
+    float *extra = reinterpret_cast<float *>(smem_raw + sizeof(StageSmem));
+    float *gsh_s = ONE_VIEW ? sm.sh : extra;
     const int n = p.g.n;
     const int base = blockIdx.x * kProjBlock;
     const int rows = min(kProjBlock, n - base);
     constexpr int nc = (DEG + 1) * (DEG + 1), nc3 = 3 * nc, shs = DEG == 3 ? kShStride3 : nc3;
     if (!ONE_VIEW)
         for (int j = threadIdx.x; j < kProjBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
-    stage_params(p.g, base, rows, sm);
+    if (ONE_VIEW)
+        stage_params(p.g, base, rows, sm, p.grad2d, 12, extra);
+    else
+        stage_params(p.g, base, rows, sm);
     const int t = threadIdx.x;
     const float lp = p.cfg.lowpass;
     float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gn[3] = {0, 0, 0};
@@ -802,7 +813,8 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project_bwd(ProjBwdLaunch p) 
         bool wrote = false;
         for (int v = 0; v < p.n_views; ++v) {
             const size_t vi = (size_t)v * n + i;
-            const float4 *g4 = reinterpret_cast<const float4 *>(p.grad2d) + 3 * vi;
+            const float4 *g4 = ONE_VIEW ? reinterpret_cast<const float4 *>(extra) + 3 * t
+                                        : reinterpret_cast<const float4 *>(p.grad2d) + 3 * vi;
             const float4 a = g4[0], b = g4[1], c = g4[2];
             G2 g2;
             g2.v[0] = a.x; g2.v[1] = a.y; g2.v[2] = a.z; g2.v[3] = a.w;
@@ -932,8 +944,11 @@ __global__ void __launch_bounds__(kProjBlock) k_project_bwd_fp64(ProjBwdLaunch p
 
 }  // namespace
 
-size_t project_smem_bytes(bool separate_sh_grads) {
-    return sizeof(StageSmem) + (separate_sh_grads ? sizeof(float) * kShStride3 * kProjBlock : 0);
+// Dynamic shared memory of a projection kernel: the staged parameters, plus for the
+// adjoint either the screen-space gradient rows (one view) or SH gradient rows.
+size_t project_smem_bytes(bool bwd, bool one_view) {
+    if (!bwd) return sizeof(StageSmem);
+    return sizeof(StageSmem) + sizeof(float) * (one_view ? 12 : kShStride3) * kProjBlock;
 }
 
 // Grid of the FP64 follow-up kernels: the list length is known only on the device,
@@ -942,7 +957,7 @@ constexpr int kFp64Blocks = 148;
 
 template <int DEG>
 cudaError_t launch_project_deg(const ProjLaunch &p, cudaStream_t s) {
-    const size_t smem = project_smem_bytes(false);
+    const size_t smem = project_smem_bytes(false, true);
     cudaError_t e = cudaFuncSetAttribute(k_project<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_project<DEG><<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
@@ -951,7 +966,7 @@ cudaError_t launch_project_deg(const ProjLaunch &p, cudaStream_t s) {
 
 template <int DEG, bool ONE_VIEW>
 cudaError_t launch_project_bwd_deg(const ProjBwdLaunch &p, cudaStream_t s) {
-    const size_t smem = project_smem_bytes(!ONE_VIEW);
+    const size_t smem = project_smem_bytes(true, ONE_VIEW);
     cudaError_t e = cudaFuncSetAttribute(k_project_bwd<DEG, ONE_VIEW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
