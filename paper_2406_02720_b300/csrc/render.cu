@@ -248,20 +248,29 @@ __device__ __forceinline__ TileInfo tile_info(const RenderLaunch &p, int gtile) 
 
 // ---- forward -------------------------------------------------------------------------
 // Pixel of a thread: warp w covers the 8x4 block (w % (TW/8), w / (TW/8)) of the tile.
+// With SPLIT blocks per tile, block `part` covers rows [part, part + 1) * TH / SPLIT.
 template <int TW>
-__device__ __forceinline__ void warp_block(const TileInfo &ti, int TH_, int &bx, int &by) {
+__device__ __forceinline__ void warp_block(const TileInfo &ti, int TH_, int row0, int &bx, int &by) {
     const int warp = threadIdx.x >> 5;
     bx = ti.tx * TW + (warp % (TW / 8)) * 8;
-    by = ti.ty * TH_ + (warp / (TW / 8)) * 4;
+    by = ti.ty * TH_ + row0 + (warp / (TW / 8)) * 4;
 }
 
+// Blocks per tile: each stages the tile's whole list for its own rows.  Fewer warps
+// per block wait for one another at the batch barriers, at the price of staging each
+// list once per block.  Measured at 3M splats, 1080p, 16x16 tiles: forward 0.726 ms
+// with 2 blocks per tile vs 0.731 with 1; backward 1.411 ms with 1 vs 1.447 with 2.
+template <bool FWD, int TW, int TH>
+constexpr int kSplit = (FWD && TW * TH >= 256) ? 2 : 1;
+
 template <int TW, int TH, int BATCH, bool COUNT>
-__device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s) {
-    constexpr int NT = TW * TH;
+__device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH> &s) {
+    constexpr int SPLIT = kSplit<true, TW, TH>;
+    constexpr int NT = TW * TH / SPLIT;
     const int tid = threadIdx.x, lane = tid & 31;
     const TileInfo ti = tile_info<TW, TH>(p, gtile);
     int bx, by;
-    warp_block<TW>(ti, TH, bx, by);
+    warp_block<TW>(ti, TH, part * (TH / SPLIT), bx, by);
     const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < ti.W && py < ti.H;
     // tile-local coordinates (pixel centres at i + 1/2)
@@ -349,13 +358,14 @@ __device__ __forceinline__ void atomic_add12(float *dst, const float g[12]) {
 }
 
 template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
-__device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, Batch<BATCH> &s,
+__device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH> &s,
                                                 uint32_t &s_maxlast) {
-    constexpr int NT = TW * TH;
+    constexpr int SPLIT = kSplit<false, TW, TH>;
+    constexpr int NT = TW * TH / SPLIT;
     const int tid = threadIdx.x, lane = tid & 31;
     const TileInfo ti = tile_info<TW, TH>(p, gtile);
     int bx, by;
-    warp_block<TW>(ti, TH, bx, by);
+    warp_block<TW>(ti, TH, part * (TH / SPLIT), bx, by);
     const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < ti.W && py < ti.H;
     // tile-local coordinates (pixel centres at i + 1/2)
@@ -494,10 +504,12 @@ struct Queue {
 };
 
 template <int TW, int TH, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 5>)) k_render_fwd(RenderLaunch p) {
+__global__ void __launch_bounds__(TW *TH / kSplit<true, TW, TH>, (kMinBlocks<TW * TH / kSplit<true, TW, TH>, 5>))
+    k_render_fwd(RenderLaunch p) {
+    constexpr int SPLIT = kSplit<true, TW, TH>;
     __shared__ Batch<BATCH> s;
     if (!p.cfg.persistent) {
-        render_tile_fwd<TW, TH, BATCH, COUNT>(p, blockIdx.x, s);
+        render_tile_fwd<TW, TH, BATCH, COUNT>(p, blockIdx.x / SPLIT, blockIdx.x % SPLIT, s);
         return;
     }
     Queue *q = reinterpret_cast<Queue *>(p.ws);
@@ -507,18 +519,20 @@ __global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 5>)) k_render_fwd
         if (threadIdx.x == 0) s_item = atomicAdd(&q->counter_fwd, 1u);
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= (uint32_t)p.vt.total_tiles) break;
-        render_tile_fwd<TW, TH, BATCH, COUNT>(p, (int)order[item], s);
+        if (item >= (uint32_t)p.vt.total_tiles * SPLIT) break;
+        render_tile_fwd<TW, TH, BATCH, COUNT>(p, (int)order[item / SPLIT], (int)(item % SPLIT), s);
         __syncthreads();
     }
 }
 
 template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
-__global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 4>)) k_render_bwd(RenderLaunch p) {
+__global__ void __launch_bounds__(TW *TH / kSplit<false, TW, TH>, (kMinBlocks<TW * TH / kSplit<false, TW, TH>, 4>))
+    k_render_bwd(RenderLaunch p) {
+    constexpr int SPLIT = kSplit<false, TW, TH>;
     __shared__ Batch<BATCH> s;
     __shared__ uint32_t s_maxlast;
     if (!p.cfg.persistent) {
-        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, blockIdx.x, s, s_maxlast);
+        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, blockIdx.x / SPLIT, blockIdx.x % SPLIT, s, s_maxlast);
         return;
     }
     Queue *q = reinterpret_cast<Queue *>(p.ws);
@@ -528,8 +542,8 @@ __global__ void __launch_bounds__(TW *TH, (kMinBlocks<TW * TH, 4>)) k_render_bwd
         if (threadIdx.x == 0) s_item = atomicAdd(&q->counter_bwd, 1u);
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= (uint32_t)p.vt.total_tiles) break;
-        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, (int)order[item], s, s_maxlast);
+        if (item >= (uint32_t)p.vt.total_tiles * SPLIT) break;
+        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, (int)order[item / SPLIT], (int)(item % SPLIT), s, s_maxlast);
         __syncthreads();
     }
 }
@@ -569,17 +583,19 @@ __global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, 
 template <int TW, int TH, int BATCH, bool FWD, bool COUNT, bool PLAIN>
 cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
     auto kern = FWD ? k_render_fwd<TW, TH, BATCH, COUNT> : k_render_bwd<TW, TH, BATCH, COUNT, PLAIN>;
+    constexpr int SPLIT = kSplit<FWD, TW, TH>, NT = TW * TH / SPLIT;
+    const int items = p.vt.total_tiles * SPLIT;
     if (!p.cfg.persistent) {
-        kern<<<p.vt.total_tiles, TW * TH, 0, s>>>(p);
+        kern<<<items, NT, 0, s>>>(p);
         return cudaGetLastError();
     }
     static int blocks = 0;
     if (!blocks) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TW * TH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
         blocks = num_sms() * std::max(occ, 1);
     }
-    kern<<<std::min(blocks, p.vt.total_tiles), TW * TH, 0, s>>>(p);
+    kern<<<std::min(blocks, items), NT, 0, s>>>(p);
     return cudaGetLastError();
 }
 
