@@ -65,7 +65,8 @@ def test_binning_bit_exact(cuda_ok, tile):
     assert np.array_equal(out["ranges"], ref["ranges"])
 
 
-@pytest.mark.parametrize("tile,batch", [((16, 16), 0), ((8, 8), 32), ((32, 8), 128), ((16, 16), 64)])
+@pytest.mark.parametrize("tile,batch", [((16, 16), 0), ((8, 8), 32), ((32, 8), 128), ((16, 16), 64),
+                                        ((16, 16), 512)])
 def test_forward_image_ragged(cuda_ok, tile, batch):
     sc, cams = _ragged_scene()
     out = gpu_render(sc, cams, tile=tile, batch=batch)
