@@ -324,6 +324,32 @@ def alu_work(stats, key):
     return fp32, mufu
 
 
+# DRAM bytes per launch of a kernel, from its committed ncu summary, valid only while
+# the kernel source is the one the summary was captured from (sha256 recorded there).
+PROFILE_OF = {"render_bwd": ("profiles/ncu_render_bwd_3M_1080p.md", "paper_2406_02720_b300/csrc/render.cu"),
+              "render_fwd": ("profiles/ncu_render_fwd_3M_1080p.md", "paper_2406_02720_b300/csrc/render.cu")}
+
+
+def profiled_traffic(phase):
+    import hashlib
+    if phase not in PROFILE_OF:
+        return None
+    prof, src = (os.path.join(ROOT, x) for x in PROFILE_OF[phase])
+    try:
+        text = open(prof).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip().lstrip("-* ")] = v.strip()
+    if vals.get("source_sha256") != digest or "traffic_bytes_per_launch" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
+
+
 def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
@@ -347,7 +373,7 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
         else:
             out.update({"bound": "alu", "achieved": mufu / t / 1e12, "peak": mufu_peak, "unit": "T MUFU-op/s",
                         "frac": f_mufu})
-        out.update({"traffic": None, "frac_fp32": f_fp32, "frac_mufu": f_mufu,
+        out.update({"traffic": profiled_traffic(dom), "frac_fp32": f_fp32, "frac_mufu": f_mufu,
                     "note": f"peak from 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz; algorithmic ops "
                             "= counted events x ops per event"})
     else:

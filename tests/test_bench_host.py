@@ -92,3 +92,18 @@ def test_reference_arm_line_on_a_small_scene(monkeypatch):
     assert line["higher_is_better"] is True and line["steps"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_profiled_traffic_needs_the_profiled_source(tmp_path, monkeypatch):
+    import hashlib
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    prof = tmp_path / "p.md"
+    digest = hashlib.sha256(b"kernel v1").hexdigest()
+    prof.write_text(f"# summary\n- source_sha256: {digest}\n- traffic_bytes_per_launch: 377340672\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.PROFILE_OF, "render_bwd", ("p.md", "k.cu"))
+    assert bench.profiled_traffic("render_bwd") == 377340672.0
+    src.write_text("kernel v2")                      # the kernel changed since the capture
+    assert bench.profiled_traffic("render_bwd") is None
+    assert bench.profiled_traffic("bin") is None
