@@ -36,7 +36,7 @@ class OrCamera(ctypes.Structure):
 
 class OrOpts(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("sh_degree", c_int),
-                ("fov_clamp", c_int), ("plain", c_int), ("lowpass", c_double)]
+                ("fov_clamp", c_int), ("plain", c_int), ("rect_mode", c_int), ("lowpass", c_double)]
 
 
 _LIB = None
@@ -50,7 +50,7 @@ def lib():
         dp, fp, ip = POINTER(c_double), POINTER(c_float), POINTER(c_int)
         L.or_abi_version.restype = c_int
         L.or_num_threads.restype = c_int
-        L.or_project.argtypes = [c_int, dp, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts),
+        L.or_project.argtypes = [c_int, dp, dp, dp, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts),
                                  ip, fp, fp, ip, ip, fp, fp, dp, dp, dp, dp, dp]
         L.or_bin.argtypes = [c_int, ip, ip, fp, c_int, c_int, POINTER(c_ubyte), c_long,
                              POINTER(c_uint64), POINTER(c_uint32), POINTER(c_uint32),
@@ -98,8 +98,9 @@ def make_camera(cam) -> OrCamera:
     return c
 
 
-def make_opts(tile=(16, 16), sh_degree=0, lowpass=0.3, plain=False, fov_clamp=True) -> OrOpts:
+def make_opts(tile=(16, 16), sh_degree=0, lowpass=0.3, plain=False, fov_clamp=True, rect_mode=0) -> OrOpts:
     o = OrOpts()
+    o.rect_mode = int(rect_mode)
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     o.sh_degree = int(sh_degree)
     o.fov_clamp = 1 if fov_clamp else 0
@@ -122,11 +123,12 @@ def grid(cam, tile):
     return tx, ty
 
 
-def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True):
-    """Per-splat projection (Eq. 2-5, 7-8; SH colour), plus canonical binning fields."""
+def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0):
+    """Per-splat projection (Eq. 2-5, 7-8; SH colour), plus canonical binning fields.
+    rect_mode 0: the 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4)."""
     s = _scene64(sc)
     n = s["means"].shape[0]
-    o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp)
+    o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp, rect_mode)
     c = make_camera(cam)
     out = dict(mode=np.zeros(n, np.int32), depth=np.zeros(n, np.float32),
                radius=np.zeros(n, np.float32), rect=np.zeros((n, 4), np.int32),
@@ -136,8 +138,8 @@ def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True):
                var_terms=np.zeros((n, 2)))
     fp, dp, ip = c_float, c_double, c_int
     lib().or_project(n, _p(s["means"], dp), _p(s["scales"], dp), _p(s["quats"], dp),
-                     _p(s["normals"], dp), _p(s["sh"], dp), ctypes.byref(c), ctypes.byref(o),
-                     _p(out["mode"], ip), _p(out["depth"], fp), _p(out["radius"], fp),
+                     _p(s["normals"], dp), _p(s["sh"], dp), _p(s["opac1"], dp), _p(s["opac2"], dp),
+                     ctypes.byref(c), ctypes.byref(o), _p(out["mode"], ip), _p(out["depth"], fp), _p(out["radius"], fp),
                      _p(out["rect"], ip), _p(out["tiles"], ip), _p(out["canon_abc"], fp),
                      _p(out["canon_mu"], fp), _p(out["mu2"], dp), _p(out["conic"], dp),
                      _p(out["wp"], dp), _p(out["rgb"], dp), _p(out["var_terms"], dp))
@@ -174,7 +176,7 @@ def bin_pairs(proj, cam, tile=(16, 16), tile_mask=None):
 
 
 def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, tile_mask=None,
-           proj=None, bins=None):
+           proj=None, bins=None, rect_mode=0):
     """Forward image: front-to-back compositing of the Eq. 10 pair weights over each
     tile's depth-sorted list (3-sigma tile culling, 1/255 floor, 0.99 clamp, 1e-4 stop).
 
@@ -182,7 +184,7 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     into margin_a for the 1/255 floor and margin_T for the 1e-4 stop, with n_comp the
     number of composited splats) and the projection/binning intermediates."""
     if proj is None:
-        proj = project(sc, cam, tile, lowpass, fov_clamp)
+        proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     W, H = int(cam.width), int(cam.height)

@@ -50,6 +50,7 @@ typedef struct {
     int sh_degree;
     int fov_clamp;   /* 1: clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS convention) */
     int plain;       /* 1: plain 3D-GS, alpha = alpha1 * hat G (P unused)           */
+    int rect_mode;   /* 0: 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4) */
     double lowpass;  /* l added to the diagonal of hat Sigma (3D-GS uses 0.3)        */
 } or_opts;
 
@@ -59,7 +60,7 @@ enum { OR_CULLED = 0, OR_NORMAL = 1, OR_STEP = 2, OR_HALF = 3 };
 #define OR_ALPHA_MAX 0.99
 #define OR_T_MIN 1e-4
 
-int or_abi_version(void) { return 3; }
+int or_abi_version(void) { return 4; }
 
 int or_num_threads(void)
 {
@@ -85,6 +86,7 @@ typedef struct {
 } canon_t;
 
 static void canon_bin(const double *mean, const double *scale, const double *quat,
+                      const double *normal, double op1, double op2,
                       const or_camera *cam, const or_opts *o, canon_t *out)
 {
     float m0 = (float)mean[0], m1 = (float)mean[1], m2 = (float)mean[2];
@@ -171,18 +173,18 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
             P[i][k] = acc + M[i][2] * L[2][k];
         }
 
-    /* 10. hat Sigma = P P^T + l I */
-    float a = P[0][0] * P[0][0];
-    a = a + P[0][1] * P[0][1];
-    a = a + P[0][2] * P[0][2];
-    a = a + lp;
+    /* 10. hat Sigma = P P^T + l I  (A0, C0: the diagonal before the low-pass) */
+    float A0 = P[0][0] * P[0][0];
+    A0 = A0 + P[0][1] * P[0][1];
+    A0 = A0 + P[0][2] * P[0][2];
+    float a = A0 + lp;
     float b = P[0][0] * P[1][0];
     b = b + P[0][1] * P[1][1];
     b = b + P[0][2] * P[1][2];
-    float c = P[1][0] * P[1][0];
-    c = c + P[1][1] * P[1][1];
-    c = c + P[1][2] * P[1][2];
-    c = c + lp;
+    float C0 = P[1][0] * P[1][0];
+    C0 = C0 + P[1][1] * P[1][1];
+    C0 = C0 + P[1][2] * P[1][2];
+    float c = C0 + lp;
     out->a = a; out->b = b; out->c = c;
 
     /* 11. determinant cull */
@@ -202,14 +204,75 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
     /* 14. finiteness cull */
     if (!(isfinite(mux) && isfinite(muy) && isfinite(r))) return;
 
-    /* 15. tile rect, clamped to the grid */
+    /* 15. extents towards -x, +x, -y, +y: the 3-sigma radius r (3D-GS), or per half */
+    float ex0 = r, ex1 = r, ey0 = r, ey1 = r;
+    if (o->rect_mode == 1) {
+        /* 15a. Support of the 3-sigma half-ellipsoid {|L^-1 (x - mu)| <= 3, n.(x - mu) >= 0}
+         * under the affine projection M, in direction e (1-sigma, without the low-pass):
+         * sqrt(e^T P P^T e) if the whole ellipsoid's extreme point in that direction lies on
+         * the kept side (sign of k.e, k = P L^T n^), else the same for the cut ellipse of
+         * the splitting plane, e^T P P^T e - (k.e)^2 / |L^T n^|^2.                       */
+        float K0 = 0.0f, K1 = 0.0f, Ar = A0, Cr = C0;
+        float nx = (float)normal[0], ny = (float)normal[1], nz = (float)normal[2];
+        float nn = nx * nx;
+        nn = nn + ny * ny;
+        nn = nn + nz * nz;
+        if (nn >= 1e-24f) {
+            float nl = sqrtf(nn);
+            float h0 = nx / nl, h1 = ny / nl, h2 = nz / nl;
+            float u[3];
+            for (int k = 0; k < 3; ++k) {
+                float acc = L[0][k] * h0;
+                acc = acc + L[1][k] * h1;
+                u[k] = acc + L[2][k] * h2;
+            }
+            float vs = u[0] * u[0];
+            vs = vs + u[1] * u[1];
+            vs = vs + u[2] * u[2];
+            K0 = P[0][0] * u[0];
+            K0 = K0 + P[0][1] * u[1];
+            K0 = K0 + P[0][2] * u[2];
+            K1 = P[1][0] * u[0];
+            K1 = K1 + P[1][1] * u[1];
+            K1 = K1 + P[1][2] * u[2];
+            if (vs > 0.0f) {
+                Ar = fmaxf(0.0f, A0 - (K0 * K0) / vs);
+                Cr = fmaxf(0.0f, C0 - (K1 * K1) / vs);
+            }
+        }
+        /* 15b. a half is splatted when its opacity reaches the 1/255 floor (as binary32) */
+        float amin = (float)(1.0 / 255.0);
+        int keep1 = (float)op1 >= amin, keep2 = (float)op2 >= amin;
+        if (!keep1 && !keep2) return;
+        float hxp = 0.0f, hxm = 0.0f, hyp = 0.0f, hym = 0.0f;
+        if (keep1) {          /* side n.(x - mu) >= 0 */
+            hxp = fmaxf(hxp, K0 >= 0.0f ? A0 : Ar);
+            hxm = fmaxf(hxm, K0 <= 0.0f ? A0 : Ar);
+            hyp = fmaxf(hyp, K1 >= 0.0f ? C0 : Cr);
+            hym = fmaxf(hym, K1 <= 0.0f ? C0 : Cr);
+        }
+        if (keep2) {          /* side n.(x - mu) <= 0 */
+            hxp = fmaxf(hxp, K0 <= 0.0f ? A0 : Ar);
+            hxm = fmaxf(hxm, K0 >= 0.0f ? A0 : Ar);
+            hyp = fmaxf(hyp, K1 <= 0.0f ? C0 : Cr);
+            hym = fmaxf(hym, K1 >= 0.0f ? C0 : Cr);
+        }
+        /* 15c. 3-sigma extents with the low-pass added in quadrature */
+        ex1 = 3.0f * sqrtf(hxp + lp);
+        ex0 = 3.0f * sqrtf(hxm + lp);
+        ey1 = 3.0f * sqrtf(hyp + lp);
+        ey0 = 3.0f * sqrtf(hym + lp);
+        if (!(isfinite(ex0) && isfinite(ex1) && isfinite(ey0) && isfinite(ey1))) return;
+    }
+
+    /* 16. tile rect, clamped to the grid */
     int tiles_x = (cam->width + o->tile_w - 1) / o->tile_w;
     int tiles_y = (cam->height + o->tile_h - 1) / o->tile_h;
     float tw = (float)o->tile_w, th = (float)o->tile_h;
-    float fx0 = floorf((mux - r) / tw);
-    float fx1 = floorf((mux + r) / tw) + 1.0f;
-    float fy0 = floorf((muy - r) / th);
-    float fy1 = floorf((muy + r) / th) + 1.0f;
+    float fx0 = floorf((mux - ex0) / tw);
+    float fx1 = floorf((mux + ex1) / tw) + 1.0f;
+    float fy0 = floorf((muy - ey0) / th);
+    float fy1 = floorf((muy + ey1) / th) + 1.0f;
     fx0 = fminf(fmaxf(fx0, 0.0f), (float)tiles_x);
     fx1 = fminf(fmaxf(fx1, 0.0f), (float)tiles_x);
     fy0 = fminf(fmaxf(fy0, 0.0f), (float)tiles_y);
@@ -437,7 +500,7 @@ static double half_fraction(const fwd_t *f, double dx, double dy, double *margin
 /* Projection of all splats: canonical binning fields + FP64 continuous ones. */
 /* ------------------------------------------------------------------------ */
 int or_project(int n, const double *means, const double *scales, const double *quats,
-               const double *normals, const double *sh,
+               const double *normals, const double *sh, const double *op1, const double *op2,
                const or_camera *cam, const or_opts *o,
                int *mode, float *depth, float *radius, int *rect, int *tiles,
                float *canon_abc, float *canon_mu,
@@ -447,7 +510,7 @@ int or_project(int n, const double *means, const double *scales, const double *q
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
         canon_t cb;
-        canon_bin(means + 3 * i, scales + 3 * i, quats + 4 * i, cam, o, &cb);
+        canon_bin(means + 3 * i, scales + 3 * i, quats + 4 * i, normals + 3 * i, op1[i], op2[i], cam, o, &cb);
         depth[i] = cb.depth;
         radius[i] = cb.radius;
         for (int j = 0; j < 4; ++j) rect[4 * i + j] = cb.rect[j];
