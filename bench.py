@@ -250,6 +250,8 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e, "e2e_params_over_pcie": e2e_full, "gpu_launches": launches * args.steps,
     }
+    if args.rect_modes:
+        result["rect_mode_1"] = run_rect_mode1(args, dev, g, dL, rast, n_pairs)
     if args.sweep:
         result["sweep"] = run_sweep(args, dev)
     if args.multiview:
@@ -576,6 +578,35 @@ def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_00
     return out
 
 
+def run_rect_mode1(args, dev, g, dL, rast0, pairs0):
+    """The same step with the per-half valid regions of Sec. 3.4 as tile rectangles
+    (hgs_config.rect_mode = 1): time, pair count, and the PSNR of its image against the
+    3-sigma-square image of the main run (the two rules differ where a splat reaches
+    beyond its 3-sigma ellipse)."""
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300.multiview import time_replays
+    from paper_2406_02720_b300.rasterizer import Gaussians, GraphStep, Rasterizer
+    img0 = rast0.images()[0].clone()
+    sc, cams, _ = _scene(args)
+    cfg = H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch, persistent=args.persistent, rect_mode=1)
+    r = Rasterizer(cams, sc.n, cfg, device=dev)
+    r.forward(g)
+    pairs = int(r.num_pairs.item())
+    r._alloc_pairs(int(pairs * 1.05) + 4096)
+    step = GraphStep(r, g, dL, Gaussians.empty_like(g))
+    ms = time_replays(step, args.sweep_steps * 5)
+    if r.read_status():
+        raise RuntimeError("device status in the rect_mode 1 step")
+    r.forward(g)
+    mse = float(torch.mean((r.images()[0] - img0) ** 2).item())
+    pix = cams[0].width * cams[0].height
+    del step, r
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms, "Mpixel_per_s": pix / (ms * 1e3), "pairs": pairs, "pairs_rect_mode_0": pairs0,
+            "psnr_vs_rect_mode_0_db": 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")}
+
+
 # ---- CPU oracle (reported baseline / reference arm) -----------------------------------------
 class OracleSample:
     """A bounded sample of the fwd+bwd step for the FP64 oracle.  The per-splat phases
@@ -694,6 +725,8 @@ def main(argv=None):
     ap.add_argument("--mv-n", type=int, default=1_000_000)
     ap.add_argument("--mv-steps", type=int, default=10)
     ap.add_argument("--sweep", action="store_true", help="also time the stress sweep (100k..6M splats)")
+    ap.add_argument("--no-rect-modes", dest="rect_modes", action="store_false",
+                    help="skip the step with per-half tile rectangles (rect_mode 1)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)

@@ -110,7 +110,16 @@ typedef struct {
  *                    0 = one thread block per tile
  *   accumulate     : 1 = hgs_project_bwd / hgs_render_bwd add into the
  *                    gradient buffers instead of overwriting them (to sum
- *                    gradients over several calls, e.g. one call per view)   */
+ *                    gradients over several calls, e.g. one call per view)
+ *   rect_mode      : tiles a splat is binned into.  0 = the square of half-side
+ *                    ceil(3 sqrt(lambda_max)) (3D-GS).  1 = the valid region of
+ *                    each half (Sec. 3.4): the bounding box, under the projection,
+ *                    of the 3-sigma half-ellipsoid of every half whose opacity
+ *                    reaches 1/255 (the whole ellipse's tangent edges where the
+ *                    half's outer surface faces that way, the splitting plane's
+ *                    cut ellipse elsewhere; low-pass added in quadrature); a splat
+ *                    with both halves below 1/255 is culled.  Mode 1 changes the
+ *                    image where a splat reached beyond its 3-sigma ellipse. */
 typedef struct {
     int tile_w, tile_h;
     int batch;
@@ -119,6 +128,7 @@ typedef struct {
     int plain;
     int persistent;
     int accumulate;
+    int rect_mode;
 } hgs_config;
 
 /* Per-(view, splat) projected records written by hgs_project, [n_views*n] rows.

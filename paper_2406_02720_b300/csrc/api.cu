@@ -36,7 +36,8 @@ bool cfg_ok(const hgs_config *c) {
                        (c->tile_w == 32 && c->tile_h == 8);
     const bool batch = c->batch == 0 || c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256 ||
                        c->batch == 512;
-    return shape && batch && isfinite(c->lowpass) && c->lowpass >= 0.0f;
+    const bool rect = c->rect_mode == 0 || c->rect_mode == 1;
+    return shape && batch && rect && isfinite(c->lowpass) && c->lowpass >= 0.0f;
 }
 
 hgs_status build_views(const hgs_camera *cams, int nv, const hgs_config *cfg, ViewTable *vt) {

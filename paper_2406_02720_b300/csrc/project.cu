@@ -111,8 +111,9 @@ struct Canon {
 
 // Binning fields in the fixed FP32 order (one IEEE op per step).
 __device__ __forceinline__ void canon_project(const float m[3], const float s[3], const float q[4],
+                                              const float nrm[3], float op1, float op2,
                                               const hgs_camera &cam, float lp, int fov_clamp,
-                                              int tw, int th, Canon &o) {
+                                              int tw, int th, int rect_mode, Canon &o) {
     o.culled = true;
     o.tiles = 0;
     o.rect[0] = o.rect[1] = o.rect[2] = o.rect[3] = 0;
@@ -182,18 +183,18 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
             acc = fa(acc, fm(M[i][1], o.L[1][k]));
             o.P[i][k] = fa(acc, fm(M[i][2], o.L[2][k]));
         }
-    // 10. hat Sigma
-    float a = fm(o.P[0][0], o.P[0][0]);
-    a = fa(a, fm(o.P[0][1], o.P[0][1]));
-    a = fa(a, fm(o.P[0][2], o.P[0][2]));
-    a = fa(a, lp);
+    // 10. hat Sigma (A0, C0: the diagonal before the low-pass)
+    float A0 = fm(o.P[0][0], o.P[0][0]);
+    A0 = fa(A0, fm(o.P[0][1], o.P[0][1]));
+    A0 = fa(A0, fm(o.P[0][2], o.P[0][2]));
+    const float a = fa(A0, lp);
     float b = fm(o.P[0][0], o.P[1][0]);
     b = fa(b, fm(o.P[0][1], o.P[1][1]));
     b = fa(b, fm(o.P[0][2], o.P[1][2]));
-    float c = fm(o.P[1][0], o.P[1][0]);
-    c = fa(c, fm(o.P[1][1], o.P[1][1]));
-    c = fa(c, fm(o.P[1][2], o.P[1][2]));
-    c = fa(c, lp);
+    float C0 = fm(o.P[1][0], o.P[1][0]);
+    C0 = fa(C0, fm(o.P[1][1], o.P[1][1]));
+    C0 = fa(C0, fm(o.P[1][2], o.P[1][2]));
+    const float c = fa(C0, lp);
     o.a = a; o.b = b; o.c = c;
     // 11. determinant cull
     float det = fs(fm(a, c), fm(b, b));
@@ -209,13 +210,71 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     o.mux = mux; o.muy = muy;
     // 14. finiteness
     if (!(isfinite(mux) && isfinite(muy) && isfinite(r))) return;
-    // 15. tile rect
+    // 15. extents towards -x, +x, -y, +y: the 3-sigma radius (3D-GS), or per half
+    float ex0 = r, ex1 = r, ey0 = r, ey1 = r;
+    if (rect_mode == 1) {
+        // 15a. 1-sigma support of each half under the projection, without the low-pass:
+        // the whole ellipse (A0, C0) where the half's outer edge faces that way (sign of
+        // k = P L^T n^), else the cut ellipse of the splitting plane (Ar, Cr)
+        float K0 = 0.0f, K1 = 0.0f, Ar = A0, Cr = C0;
+        float nn = fm(nrm[0], nrm[0]);
+        nn = fa(nn, fm(nrm[1], nrm[1]));
+        nn = fa(nn, fm(nrm[2], nrm[2]));
+        if (nn >= 1e-24f) {
+            const float nl = __fsqrt_rn(nn);
+            const float h0 = fdv(nrm[0], nl), h1 = fdv(nrm[1], nl), h2 = fdv(nrm[2], nl);
+            float u[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float acc = fm(o.L[0][k], h0);
+                acc = fa(acc, fm(o.L[1][k], h1));
+                u[k] = fa(acc, fm(o.L[2][k], h2));
+            }
+            float vs = fm(u[0], u[0]);
+            vs = fa(vs, fm(u[1], u[1]));
+            vs = fa(vs, fm(u[2], u[2]));
+            K0 = fm(o.P[0][0], u[0]);
+            K0 = fa(K0, fm(o.P[0][1], u[1]));
+            K0 = fa(K0, fm(o.P[0][2], u[2]));
+            K1 = fm(o.P[1][0], u[0]);
+            K1 = fa(K1, fm(o.P[1][1], u[1]));
+            K1 = fa(K1, fm(o.P[1][2], u[2]));
+            if (vs > 0.0f) {
+                Ar = fmaxf(0.0f, fs(A0, fdv(fm(K0, K0), vs)));
+                Cr = fmaxf(0.0f, fs(C0, fdv(fm(K1, K1), vs)));
+            }
+        }
+        // 15b. a half is splatted when its opacity reaches the 1/255 floor
+        const float amin = 1.0f / 255.0f;
+        const bool keep1 = op1 >= amin, keep2 = op2 >= amin;
+        if (!keep1 && !keep2) return;
+        float hxp = 0.0f, hxm = 0.0f, hyp = 0.0f, hym = 0.0f;
+        if (keep1) {   // side n.(x - mu) >= 0
+            hxp = fmaxf(hxp, K0 >= 0.0f ? A0 : Ar);
+            hxm = fmaxf(hxm, K0 <= 0.0f ? A0 : Ar);
+            hyp = fmaxf(hyp, K1 >= 0.0f ? C0 : Cr);
+            hym = fmaxf(hym, K1 <= 0.0f ? C0 : Cr);
+        }
+        if (keep2) {   // side n.(x - mu) <= 0
+            hxp = fmaxf(hxp, K0 <= 0.0f ? A0 : Ar);
+            hxm = fmaxf(hxm, K0 >= 0.0f ? A0 : Ar);
+            hyp = fmaxf(hyp, K1 <= 0.0f ? C0 : Cr);
+            hym = fmaxf(hym, K1 >= 0.0f ? C0 : Cr);
+        }
+        // 15c. 3-sigma extents with the low-pass in quadrature
+        ex1 = fm(3.0f, __fsqrt_rn(fa(hxp, lp)));
+        ex0 = fm(3.0f, __fsqrt_rn(fa(hxm, lp)));
+        ey1 = fm(3.0f, __fsqrt_rn(fa(hyp, lp)));
+        ey0 = fm(3.0f, __fsqrt_rn(fa(hym, lp)));
+        if (!(isfinite(ex0) && isfinite(ex1) && isfinite(ey0) && isfinite(ey1))) return;
+    }
+    // 16. tile rect
     int tiles_x = div_up(cam.width, tw), tiles_y = div_up(cam.height, th);
     float ftw = (float)tw, fth = (float)th;
-    float x0 = floorf(fdv(fs(mux, r), ftw));
-    float x1 = fa(floorf(fdv(fa(mux, r), ftw)), 1.0f);
-    float y0 = floorf(fdv(fs(muy, r), fth));
-    float y1 = fa(floorf(fdv(fa(muy, r), fth)), 1.0f);
+    float x0 = floorf(fdv(fs(mux, ex0), ftw));
+    float x1 = fa(floorf(fdv(fa(mux, ex1), ftw)), 1.0f);
+    float y0 = floorf(fdv(fs(muy, ey0), fth));
+    float y1 = fa(floorf(fdv(fa(muy, ey1), fth)), 1.0f);
     x0 = fminf(fmaxf(x0, 0.0f), (float)tiles_x);
     x1 = fminf(fmaxf(x1, 0.0f), (float)tiles_x);
     y0 = fminf(fmaxf(y0, 0.0f), (float)tiles_y);
@@ -577,7 +636,8 @@ __global__ void __launch_bounds__(kProjBlock, 5) k_project(ProjLaunch p) {
         const hgs_camera &cam = p.cams[v];
         const size_t vi = (size_t)v * n + i;
         Canon cb;
-        canon_project(P.m, P.s, P.q, cam, lp, p.cfg.fov_clamp, p.cfg.tile_w, p.cfg.tile_h, cb);
+        canon_project(P.m, P.s, P.q, P.n, o1, o2, cam, lp, p.cfg.fov_clamp, p.cfg.tile_w, p.cfg.tile_h,
+                      p.cfg.rect_mode, cb);
         p.out.depth[vi] = cb.depth;
         reinterpret_cast<int4 *>(p.out.rect)[vi] = make_int4(cb.rect[0], cb.rect[1], cb.rect[2], cb.rect[3]);
         p.out.tiles[vi] = cb.culled ? 0u : cb.tiles;
