@@ -140,9 +140,10 @@ typedef struct {
  *                  U = [[u11, u12], [0, u22]] is the Cholesky factor of the conic
  *                  hat Sigma^-1 = U^T U; w' = hat Sigma^-1 k / sqrt(2 v), so that
  *                  the half-plane fraction is P(d) = 1/2 erfc(-w'.d) (Eq. 8).
- *   depth  [.]     camera-space z of the mean (the sort key's low 32 bits)
+ *   depth  [.]     (16-B aligned) camera-space z of the mean (the sort key's low
+ *                  32 bits)
  *   rect   [.,4]   (16-B aligned) covered tiles [x0,x1) x [y0,y1) of the view
- *   tiles  [.]     number of covered tiles, 0 if culled
+ *   tiles  [.]     (16-B aligned) number of covered tiles, 0 if culled
  *   fp64_list [1 + n_views*n] uint32 scratch: hgs_project gathers here the
  *                  (view, splat) records whose splitting plane nearly contains
  *                  the ray (v < 1e-3 var_s) and recomputes their half-plane terms

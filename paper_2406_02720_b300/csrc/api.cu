@@ -78,7 +78,7 @@ bool proj_ok(const hgs_proj *p, long long vn, bool need_list = false) {
     if (!p) return false;
     if (vn == 0) return true;
     return p->rec && p->depth && p->rect && p->tiles && (p->fp64_list || !need_list) && aligned16(p->rec) &&
-           aligned16(p->rect) && aligned16(p->tiles);
+           aligned16(p->depth) && aligned16(p->rect) && aligned16(p->tiles);
 }
 
 hgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HGS_OK : HGS_ERR_CUDA; }

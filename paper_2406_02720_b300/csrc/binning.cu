@@ -104,13 +104,27 @@ struct Count {
 };
 
 // ---- stage 1: depth keys ------------------------------------------------------------------
+// Four (view, splat) entries a thread, with 128-bit loads and stores (vn % 4 tail
+// handled element by element).
 __global__ void __launch_bounds__(kBlock) k_depth_keys(const uint32_t *__restrict__ tiles,
                                                        const float *__restrict__ depth, long long vn,
                                                        uint32_t *__restrict__ dk, uint32_t *__restrict__ dv) {
-    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
-    if (i >= vn) return;
-    dk[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
-    dv[i] = (uint32_t)i;
+    const long long i0 = 4 * ((long long)blockIdx.x * kBlock + threadIdx.x);
+    if (i0 >= vn) return;
+    if (i0 + 4 <= vn) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(tiles + i0);
+        const float4 d = *reinterpret_cast<const float4 *>(depth + i0);
+        *reinterpret_cast<uint4 *>(dk + i0) =
+            make_uint4(t.x ? __float_as_uint(d.x) : 0xffffffffu, t.y ? __float_as_uint(d.y) : 0xffffffffu,
+                       t.z ? __float_as_uint(d.z) : 0xffffffffu, t.w ? __float_as_uint(d.w) : 0xffffffffu);
+        const uint32_t b = (uint32_t)i0;
+        *reinterpret_cast<uint4 *>(dv + i0) = make_uint4(b, b + 1, b + 2, b + 3);
+    } else {
+        for (long long i = i0; i < vn; ++i) {
+            dk[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
+            dv[i] = (uint32_t)i;
+        }
+    }
 }
 
 // ---- radix pass, part 1: digit counts of every partition ---------------------------------
@@ -335,28 +349,41 @@ __global__ void __launch_bounds__(kBlock, 4) k_downsweep(DownArgs a) {
 // contiguous) and sums each chunk of kBlock splats; k_chunk_scan turns the chunk sums
 // into exclusive prefixes (64-bit: the total may exceed the pair capacity) and the
 // pair count; k_duplicate finishes the scan inside each chunk.
+// A block covers 8 chunks of kBlock splats, a warp one chunk, a thread 8 consecutive
+// splats (two 128-bit loads of the order, 8 independent gathers in flight).
+constexpr int kReducePer = 8;
+
 __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t *__restrict__ tiles,
                                                         const uint32_t *__restrict__ order, long long vn,
                                                         uint32_t *__restrict__ tiles_sorted,
                                                         unsigned long long *__restrict__ chunk_sum) {
-    __shared__ unsigned long long s_w[kBlock / 32];
-    const long long j = (long long)blockIdx.x * kBlock + threadIdx.x;
-    uint32_t t = 0;
-    if (j < vn) {
-        t = tiles[order[j]];
-        tiles_sorted[j] = t;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    // this warp's 256 splats start at `base` (chunk base / kBlock); a thread takes 8 consecutive
+    const long long base = (long long)blockIdx.x * kBlock * kReducePer + (long long)warp * 32 * kReducePer;
+    const long long i0 = base + (long long)lane * kReducePer;
+    uint32_t t[kReducePer];
+    if (i0 + kReducePer <= vn) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(order + i0);
+        const uint4 b = *reinterpret_cast<const uint4 *>(order + i0 + 4);
+        t[0] = tiles[a.x]; t[1] = tiles[a.y]; t[2] = tiles[a.z]; t[3] = tiles[a.w];
+        t[4] = tiles[b.x]; t[5] = tiles[b.y]; t[6] = tiles[b.z]; t[7] = tiles[b.w];
+        *reinterpret_cast<uint4 *>(tiles_sorted + i0) = make_uint4(t[0], t[1], t[2], t[3]);
+        *reinterpret_cast<uint4 *>(tiles_sorted + i0 + 4) = make_uint4(t[4], t[5], t[6], t[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kReducePer; ++k) {
+            t[k] = i0 + k < vn ? tiles[order[i0 + k]] : 0u;
+            if (i0 + k < vn) tiles_sorted[i0 + k] = t[k];
+        }
     }
-    unsigned long long x = t;
+    unsigned long long x = 0;
+#pragma unroll
+    for (int k = 0; k < kReducePer; ++k) x += t[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane_id() == 0) s_w[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long sum = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += s_w[w2];
-        chunk_sum[blockIdx.x] = sum;
-    }
+    // the warp's 256 splats are chunk `base / kBlock`; only existing chunks are written
+    const long long c = base / kBlock;
+    if (lane == 0 && base < vn) chunk_sum[c] = x;
 }
 
 constexpr int kChunkScanThreads = 1024;
@@ -365,7 +392,7 @@ __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(unsigned long 
                                                                   uint64_t *total_out) {
     __shared__ unsigned long long s_w[kChunkScanThreads / 32];
     __shared__ unsigned long long s_total;
-    constexpr int kPer = 4;
+    constexpr int kPer = 16;                   // one round below 16384 chunks (4.2M splats)
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     unsigned long long carry = 0;
     for (long long base = 0; base < n_chunks; base += (long long)kChunkScanThreads * kPer) {
@@ -579,7 +606,7 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
     if (vn == 0) return cudaSuccess;
 
     // stage 1: depth keys, four passes over them (the order ends in dkA/dvA)
-    k_depth_keys<<<(unsigned)((vn + kBlock - 1) / kBlock), kBlock, 0, s>>>(p.proj->tiles, p.proj->depth,
+    k_depth_keys<<<(unsigned)((vn + 4 * kBlock - 1) / (4 * kBlock)), kBlock, 0, s>>>(p.proj->tiles, p.proj->depth,
                                                                            (long long)vn, w.dkA, w.dvA);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const Count cnt_vn{vn, nullptr, vn};
@@ -592,8 +619,8 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
 
     // stage 2: pair offsets in depth order, pair emission, passes over the tile half
     const long long n_chunks = (long long)((vn + kBlock - 1) / kBlock);
-    k_scan_reduce<<<(unsigned)n_chunks, kBlock, 0, s>>>(p.proj->tiles, w.dvA, (long long)vn, w.tiles_sorted,
-                                                       w.chunk_pre);
+    k_scan_reduce<<<(unsigned)((vn + (size_t)kBlock * kReducePer - 1) / ((size_t)kBlock * kReducePer)), kBlock, 0,
+                    s>>>(p.proj->tiles, w.dvA, (long long)vn, w.tiles_sorted, w.chunk_pre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_chunk_scan<<<1, kChunkScanThreads, 0, s>>>(w.chunk_pre, n_chunks, p.num_pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -567,6 +567,7 @@ __global__ void k_queue_count(const uint32_t *ranges, int total_tiles, Queue *q)
         if (h[j]) atomicAdd(&q->bucket_count[j], h[j]);
 }
 
+// Lanes of a warp with the same bucket take consecutive slots with one atomic.
 __global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, uint32_t *order) {
     __shared__ uint32_t start[33];
     if (threadIdx.x == 0) {
@@ -574,9 +575,17 @@ __global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, 
         for (int b = 32; b >= 0; --b) { start[b] = acc; acc += q->bucket_count[b]; }
     }
     __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
-        const int b = cost_bucket(ranges, t);
-        order[start[b] + atomicAdd(&q->bucket_cursor[b], 1u)] = (uint32_t)t;
+    const int lane = threadIdx.x & 31;
+    for (int t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < total_tiles; t0 += gridDim.x * blockDim.x) {
+        const int t = t0 + lane;
+        const bool valid = t < total_tiles;
+        const int b = valid ? cost_bucket(ranges, t) : 33;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (valid && lane == leader) base = atomicAdd(&q->bucket_cursor[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) order[start[b] + base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
     }
 }
 
