@@ -4,7 +4,7 @@
 
 Workload (default): 3M half-Gaussians, SH degree 3, 1920x1080, one view, the
 scene-scale synthetic scene (50 blobs + 10% uniform, bimodal opacities).  A step
-is project -> bin (scan, keys, onesweep sort, ranges) -> composite -> adjoint
+is project -> bin (depth keys, radix sort, scan, pair emission, ranges) -> composite -> adjoint
 composite -> projection adjoint, captured once in a CUDA graph and replayed.
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
 a bounded sample of the same workload instead.

@@ -16,7 +16,7 @@
 // with cudaGetSymbolAddress; that first call should therefore come before any
 // stream capture.  All calls share the one array and it keeps the previous
 // call's contents: the binning kernels clear everything that must start at zero
-// (digit histograms, partition tickets, look-back words) at the start of each
+// (the control block with the digit totals) at the start of each
 // call, and overwrite the rest before reading it.  Calls whose work overlaps on
 // the GPU (other streams, other threads) race on the array; calls in order on
 // one stream do not.

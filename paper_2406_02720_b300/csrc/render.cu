@@ -1,8 +1,8 @@
 // Per-pixel compositing of half-Gaussian splats (A6) and its adjoint (A7).
 //
-// One thread block per tile (one thread per pixel).  The tile's depth-sorted
-// list is walked in batches that the block stages in shared memory.  For each
-// (pixel, splat) pair:
+// Blocks walk a tile's depth-sorted list in batches that they stage in shared
+// memory (the forward uses two 128-thread blocks per 16x16 tile, one per 16x8
+// half; the backward one 256-thread block).  For each (pixel, splat) pair:
 //   d = p - mu-hat,  hat G = exp(-1/2 |U d|^2), conic = U^T U  (Eq. 4-5)
 //   P = 1/2 erfc(-w'.d)                                         (Eq. 7-8)
 //   a = min(0.99, (alpha2 + (alpha1 - alpha2) P) hat G)          (Eq. 10)
@@ -20,19 +20,18 @@
 // per-splat decisions are bit-identical.
 //
 // Each warp owns an 8x4 block of the tile's pixels.  Per 32 staged splats it
-// tests the bounding box of every splat's cut-off ellipse (the pixels where
-// alpha could reach 1/255) against its block and ballots; only the hits are
-// visited.  The box is inflated past the cut-off, so culling changes no
-// per-pixel decision.
+// tests every splat's cut-off ellipse (the pixels where alpha could reach 1/255)
+// against its block with separating axes (x, y and the ellipse's minor axis) and
+// ballots; only the hits are visited.  The bounds are inflated past the cut-off,
+// so culling changes no per-pixel decision.
 //
 // The backward walks each pixel's list back to front from its last composited
 // splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i).
-// The 12 screen-space gradients of a (warp, splat) are summed with a butterfly
-// that halves the number of live values at each of its first four levels (16
-// shuffles instead of 60) and land with one 12-lane atomic instruction; a splat
-// that only one lane of the warp touches goes straight to three float4 atomics.
+// The 12 screen-space gradients of a (warp, splat) leave as per-lane float4
+// atomic adds, with one shuffle level folding lane pairs first when more than 16
+// lanes contribute.
 //
-// Persistent mode: a grid of resident blocks pops global tile ids from an
+// Persistent mode (the default): a grid of resident blocks pops tiles from an
 // atomic queue whose order is heaviest-first (bucketed by list length).
 #include <algorithm>
 
