@@ -388,31 +388,40 @@ __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t *__restri
 
 constexpr int kChunkScanThreads = 1024;
 
+// One block.  Warp w of a round scans 512 consecutive chunk sums, read row by row
+// (lane l of row i holds entry 32 i + l: every load is coalesced); the warps'
+// totals are then scanned across the block.  One round below 16384 chunks.
 __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(unsigned long long *chunk, long long n_chunks,
                                                                   uint64_t *total_out) {
     __shared__ unsigned long long s_w[kChunkScanThreads / 32];
     __shared__ unsigned long long s_total;
-    constexpr int kPer = 16;                   // one round below 16384 chunks (4.2M splats)
+    constexpr int kRows = 16, kSeg = 32 * kRows;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     unsigned long long carry = 0;
-    for (long long base = 0; base < n_chunks; base += (long long)kChunkScanThreads * kPer) {
-        const long long j0 = base + (long long)tid * kPer;
-        unsigned long long v[kPer], sum = 0;
+    for (long long base = 0; base < n_chunks; base += (long long)kChunkScanThreads * kRows) {
+        const long long seg = base + (long long)warp * kSeg;
+        unsigned long long v[kRows], ex[kRows], run = 0;
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            v[k] = j0 + k < n_chunks ? chunk[j0 + k] : 0ull;
-            sum += v[k];
+        for (int i = 0; i < kRows; ++i) {
+            const long long j = seg + 32 * i + lane;
+            v[i] = j < n_chunks ? chunk[j] : 0ull;
         }
-        unsigned long long x = sum;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        for (int i = 0; i < kRows; ++i) {
+            unsigned long long x = v[i];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            ex[i] = run + x - v[i];
+            run += __shfl_sync(0xffffffffu, x, 31);
         }
-        if (lane == 31) s_w[warp] = x;
+        if (lane == 0) s_w[warp] = run;
         __syncthreads();
         if (warp == 0) {
-            unsigned long long w = s_w[lane], wx = w;
+            const unsigned long long w = s_w[lane];
+            unsigned long long wx = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long y = __shfl_up_sync(0xffffffffu, wx, o);
@@ -422,11 +431,11 @@ __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(unsigned long 
             if (lane == 31) s_total = wx;
         }
         __syncthreads();
-        unsigned long long run = carry + s_w[warp] + x - sum;
+        const unsigned long long off = carry + s_w[warp];
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            if (j0 + k < n_chunks) chunk[j0 + k] = run;
-            run += v[k];
+        for (int i = 0; i < kRows; ++i) {
+            const long long j = seg + 32 * i + lane;
+            if (j < n_chunks) chunk[j] = off + ex[i];
         }
         carry += s_total;
         __syncthreads();
