@@ -425,9 +425,9 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 const bool cand = inside && pos < last;
                 const bool contrib = cand && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
                 if (COUNT) { c_visit += cand; c_full += (cand && ev.G >= 0.0f); c_contrib += contrib; }
+                // set in full by contributing lanes only; other lanes' values are never read
+                // (the fold below selects zero for them)
                 float gr[12];
-#pragma unroll
-                for (int f = 0; f < 12; ++f) gr[f] = 0.0f;
                 if (contrib) {
                     const float4 g0 = s.g0[k];
                     const float4 g1 = s.g1[k];
@@ -448,6 +448,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                         const float dA = dLda * ev.G;
                         if (plain) {
                             gr[7] = dA;                  // alpha = alpha1 G: nothing to alpha2 or w'
+                            gr[8] = 0.0f;
                         } else {
                             gr[7] = dA * ev.P;
                             gr[8] = dA - gr[7];
@@ -461,6 +462,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                         const float sc = dpow * kInvUScale2;
                         gr[0] = sc * (g0.z * ev.s1);
                         gr[1] = sc * (g0.w * ev.s1 + g1.x * ev.s2);
+                        gr[5] = gr[6] = 0.0f;
                         if (!plain && fabsf(g1.z) + fabsf(g1.w) < kStepDetect) {
                             const float dz = dA * g2.y * ev.e * kInvSqrtPi;
                             gr[5] = dz * dx;
@@ -468,6 +470,9 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                             gr[0] -= dz * g1.z;
                             gr[1] -= dz * g1.w;
                         }
+                    } else {
+#pragma unroll
+                        for (int f = 0; f < 9; ++f) gr[f] = 0.0f;   // a clamped at 0.99: no path to G, P
                     }
                 }
                 const unsigned any = __ballot_sync(0xffffffffu, contrib);
@@ -478,7 +483,10 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 } else {
                     if (COUNT && lane == 0) ++c_red;
 #pragma unroll
-                    for (int f = 0; f < 12; ++f) gr[f] += __shfl_xor_sync(0xffffffffu, gr[f], 16);
+                    for (int f = 0; f < 12; ++f) {
+                        const float x = contrib ? gr[f] : 0.0f;
+                        gr[f] = x + __shfl_xor_sync(0xffffffffu, x, 16);
+                    }
                     if (lane < 16 && ((any >> lane) & 0x10001u)) atomic_add12(dst, gr);
                 }
             }
