@@ -40,7 +40,6 @@
 namespace hgs {
 namespace {
 
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kUScale = 0.84932180028801907f;   // sqrt(log2(e) / 2)
 constexpr float kInvUScale2 = 1.3862943611198906f; // 1 / kUScale^2 = 2 ln 2
 constexpr float kInvSqrtPi = 0.56418958354775628f;
@@ -52,6 +51,13 @@ constexpr float kStepDetect = 1e20f;     // |w'| beyond this: step-mode splat (n
 constexpr float kAsP = 0.3275911f;
 constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f;
 constexpr float kAs4 = -1.453152027f, kAs5 = 1.061405429f;
+// Staged w' is scaled by sqrt(log2 e), so z' = w'.d gives exp(-z^2) = 2^-(z'^2) with no
+// multiply; the A&S argument absorbs the scale in its constant p.  The coefficients
+// are halved so that the polynomial gives erfc(|z|) / 2 directly.
+constexpr float kSqrtLog2e = 1.2011224087864498f;
+constexpr float kInvSqrtLog2e = 0.83255461115769775f;
+constexpr float kAsPs = kAsP * kInvSqrtLog2e;
+constexpr float kAh1 = 0.5f * kAs1, kAh2 = 0.5f * kAs2, kAh3 = 0.5f * kAs3, kAh4 = 0.5f * kAs4, kAh5 = 0.5f * kAs5;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -113,7 +119,7 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     // alpha <= amax * G < 1/255 whenever log2 G < -log2(255 amax); 1e-3 covers ex2/lg2 error
     const float qcut = amax > 0.0f ? __fadd_rn(lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : -1.0f;
     s.g0[k] = make_float4(mx, my, u11, u12);
-    s.g1[k] = make_float4(u22, qcut, r1.w, r2.x);
+    s.g1[k] = make_float4(u22, qcut, __fmul_rn(r1.w, kSqrtLog2e), __fmul_rn(r2.x, kSqrtLog2e));
     s.g2[k] = make_float4(a2, __fsub_rn(a1, a2), r2.w, r3.x);
     s.b[k] = r3.y;
     s.id[k] = id;
@@ -180,20 +186,20 @@ __device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const Batch<BAT
     const float s2 = __fmul_rn(g1.x, dy);
     const float q = __fmaf_rn(s1, s1, __fmul_rn(s2, s2));
     if (!(q <= g1.y)) { ev.G = -1.0f; return false; }
-    const float2 w = *reinterpret_cast<const float2 *>(&s.g1[k].z);  // w'x, w'y
+    const float2 w = *reinterpret_cast<const float2 *>(&s.g1[k].z);  // sqrt(log2 e) w'
     const float2 al = *reinterpret_cast<const float2 *>(&s.g2[k]);   // alpha2, alpha1 - alpha2
     const float G = ex2_approx(-q);
-    const float z = __fmaf_rn(w.x, dx, __fmul_rn(w.y, dy));
+    const float z = __fmaf_rn(w.x, dx, __fmul_rn(w.y, dy));          // sqrt(log2 e) w'.d
     const float u = fabsf(z);
-    const float t = rcp_approx(__fmaf_rn(kAsP, u, 1.0f));
-    float poly = __fmaf_rn(kAs5, t, kAs4);
-    poly = __fmaf_rn(poly, t, kAs3);
-    poly = __fmaf_rn(poly, t, kAs2);
-    poly = __fmaf_rn(poly, t, kAs1);
+    const float t = rcp_approx(__fmaf_rn(kAsPs, u, 1.0f));
+    float poly = __fmaf_rn(kAh5, t, kAh4);
+    poly = __fmaf_rn(poly, t, kAh3);
+    poly = __fmaf_rn(poly, t, kAh2);
+    poly = __fmaf_rn(poly, t, kAh1);
     poly = __fmul_rn(poly, t);
-    const float e = ex2_approx(__fmul_rn(-kLog2e, __fmul_rn(u, u)));   // exp(-z^2)
-    const float y = __fmul_rn(poly, e);                                   // erfc(|z|)
-    const float P = z >= 0.0f ? __fsub_rn(1.0f, __fmul_rn(0.5f, y)) : __fmul_rn(0.5f, y);
+    const float e = ex2_approx(-__fmul_rn(u, u));                      // exp(-(w'.d)^2)
+    const float h = __fmul_rn(poly, e);                                 // erfc(|w'.d|) / 2
+    const float P = z >= 0.0f ? __fsub_rn(1.0f, h) : h;
     const float A = __fmaf_rn(al.y, P, al.x);
     const float araw = __fmul_rn(A, G);
     ev.clamped = araw > kAlphaMax;
@@ -464,11 +470,13 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                         gr[1] = sc * (g0.w * ev.s1 + g1.x * ev.s2);
                         gr[5] = gr[6] = 0.0f;
                         if (!plain && fabsf(g1.z) + fabsf(g1.w) < kStepDetect) {
+                            // d P / d(w'.d) = exp(-(w'.d)^2) / sqrt(pi); staged w' carries sqrt(log2 e)
                             const float dz = dA * g2.y * ev.e * kInvSqrtPi;
+                            const float dzs = dz * kInvSqrtLog2e;
                             gr[5] = dz * dx;
                             gr[6] = dz * dy;
-                            gr[0] -= dz * g1.z;
-                            gr[1] -= dz * g1.w;
+                            gr[0] -= dzs * g1.z;
+                            gr[1] -= dzs * g1.w;
                         }
                     } else {
 #pragma unroll
