@@ -83,7 +83,7 @@ __device__ __forceinline__ float lg2_approx(float x) {
 
 // One staged batch of a tile's list in shared memory, a float4 record per field
 // group so that a warp-uniform visit reads a whole group with one broadcast load.
-template <int BATCH>
+template <int BATCH, bool BWD>
 struct Batch {
     float4 g0[BATCH];    // mx, my (tile-local centre), u11, u12 (Cholesky factor of the conic, x kUScale)
     float4 g1[BATCH];    // u22, qcut (skip when s1^2 + s2^2 exceeds it), w'x, w'y
@@ -91,6 +91,7 @@ struct Batch {
     float4 cu[BATCH];    // culling vs an 8x4 block centred at c: |cx-mx| <= .x, |cy-my| <= .y,
                          // |(c-mu).(.z,.w)| <= 1
     float b[BATCH];
+    float dzk[BWD ? BATCH : 1];   // backward: (alpha1 - alpha2) / sqrt(pi), 0 for a step-mode splat
     uint32_t id[BATCH];
 };
 
@@ -104,8 +105,8 @@ struct Batch {
 // n = the ellipse's minor axis, |n.(c - mu)| <= h(n) + 3.5|n_x| + 1.5|n_y|.  Every
 // bound is inflated (x1.001 + 1e-3) so that no block whose pixels pass the FP32
 // cut-off test of eval_alpha is culled.
-template <int BATCH>
-__device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH> &s, int k,
+template <int BATCH, bool BWD>
+__device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH, BWD> &s, int k,
                                       float ox, float oy, bool plain) {
     const float4 r0 = __ldg(rec + 4 * (size_t)id);
     const float4 r1 = __ldg(rec + 4 * (size_t)id + 1);
@@ -119,9 +120,12 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
     // alpha <= amax * G < 1/255 whenever log2 G < -log2(255 amax); 1e-3 covers ex2/lg2 error
     const float qcut = amax > 0.0f ? __fadd_rn(lg2_approx(__fmul_rn(255.0f, amax)), 1e-3f) : -1.0f;
     s.g0[k] = make_float4(mx, my, u11, u12);
-    s.g1[k] = make_float4(u22, qcut, __fmul_rn(r1.w, kSqrtLog2e), __fmul_rn(r2.x, kSqrtLog2e));
+    const float wx = __fmul_rn(r1.w, kSqrtLog2e), wy = __fmul_rn(r2.x, kSqrtLog2e);
+    s.g1[k] = make_float4(u22, qcut, wx, wy);
     s.g2[k] = make_float4(a2, __fsub_rn(a1, a2), r2.w, r3.x);
     s.b[k] = r3.y;
+    // d P / d(w'.d) = exp(-(w'.d)^2) / sqrt(pi); a step-mode splat (|w'| ~ 2^80) has none
+    if (BWD) s.dzk[k] = (!plain && fabsf(wx) + fabsf(wy) < kStepDetect) ? (a1 - a2) * kInvSqrtPi : 0.0f;
     s.id[k] = id;
     float4 cu = make_float4(-1.0f, -1.0f, 0.0f, 0.0f);
     if (qcut >= 0.0f) {
@@ -161,8 +165,8 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
 }
 
 // Can slot j touch the 8x4 block centred at (cx, cy)?  (conservative, see stage)
-template <int BATCH>
-__device__ __forceinline__ bool cull_hit(const Batch<BATCH> &s, int j, float cx, float cy) {
+template <class SB>
+__device__ __forceinline__ bool cull_hit(const SB &s, int j, float cx, float cy) {
     const float2 m = *reinterpret_cast<const float2 *>(&s.g0[j]);
     const float4 cu = s.cu[j];
     const float dx = cx - m.x, dy = cy - m.y;
@@ -170,14 +174,14 @@ __device__ __forceinline__ bool cull_hit(const Batch<BATCH> &s, int j, float cx,
 }
 
 struct Eval {
-    float a, G, P, A, dx, dy, e, s1, s2;
+    float a, G, P, dx, dy, e, s1, s2;
     bool clamped;
 };
 
 // The per-(pixel, splat) weight of Eq. 10; true if the splat is composited
 // (a >= 1/255).  Identical instruction sequence in forward and backward.
-template <int BATCH>
-__device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const Batch<BATCH> &s, int k, Eval &ev) {
+template <class SB>
+__device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const SB &s, int k, Eval &ev) {
     const float4 g0 = s.g0[k];
     const float2 g1 = *reinterpret_cast<const float2 *>(&s.g1[k]);   // u22, qcut
     const float dx = __fsub_rn(fpx, g0.x);
@@ -204,7 +208,7 @@ __device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const Batch<BAT
     const float araw = __fmul_rn(A, G);
     ev.clamped = araw > kAlphaMax;
     ev.a = ev.clamped ? kAlphaMax : araw;
-    ev.G = G; ev.P = P; ev.A = A; ev.dx = dx; ev.dy = dy; ev.e = e; ev.s1 = s1; ev.s2 = s2;
+    ev.G = G; ev.P = P; ev.dx = dx; ev.dy = dy; ev.e = e; ev.s1 = s1; ev.s2 = s2;
     return ev.a >= kAlphaMin;
 }
 
@@ -269,7 +273,7 @@ template <bool FWD, int TW, int TH>
 constexpr int kSplit = (FWD && TW * TH >= 256) ? 2 : 1;
 
 template <int TW, int TH, int BATCH, bool COUNT>
-__device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH> &s) {
+__device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH, false> &s) {
     constexpr int SPLIT = kSplit<true, TW, TH>;
     constexpr int NT = TW * TH / SPLIT;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -297,7 +301,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
             if (j < ti.end) {
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH>(rec, id, s, k, fox, foy, plain);
+                stage<BATCH, false>(rec, id, s, k, fox, foy, plain);
             }
         }
         __syncthreads();
@@ -305,14 +309,14 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
         bool wdone = __all_sync(0xffffffffu, done);
         for (int c = 0; c < cnt && !wdone; c += 32) {
             const int jl = c + lane;
-            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && cull_hit<BATCH>(s, jl, cxb, cyb));
+            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && cull_hit(s, jl, cxb, cyb));
             while (m) {
                 const int k = c + __ffs(m) - 1;
                 m &= m - 1;
                 if (!done) {
                     Eval ev;
                     if (COUNT) ++c_visit;
-                    const bool hit = eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+                    const bool hit = eval_alpha(fpx, fpy, s, k, ev);
                     if (COUNT && ev.G >= 0.0f) ++c_full;
                     if (hit) {
                         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
@@ -363,7 +367,7 @@ __device__ __forceinline__ void atomic_add12(float *dst, const float g[12]) {
 }
 
 template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
-__device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH> &s,
+__device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH, true> &s,
                                                 uint32_t &s_maxlast) {
     constexpr int SPLIT = kSplit<false, TW, TH>;
     constexpr int NT = TW * TH / SPLIT;
@@ -400,7 +404,9 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
     const float bgg = ti.bg[0] * g0_ + ti.bg[1] * g1_ + ti.bg[2] * g2_;
     const float TfB = Tf * bgg;             // d L / d a_i gets -T_final bg.g / (1 - a_i)
     constexpr bool plain = PLAIN;
-    float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
+    // colour composited behind the current splat, dotted with this pixel's dL/dC:
+    // (c_i - S_i).g = c_i.g - S_i.g, and S.g follows the same recurrence as S
+    float Sg = 0.0f;
     float *grad = p.grad2d;
     unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0;
     for (uint32_t bend = tile_end; bend > ti.beg;) {
@@ -411,7 +417,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
             if (j < bend) {
                 uint32_t id = p.ids[j];
                 if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH>(rec, id, s, k, fox, foy, plain);
+                stage<BATCH, true>(rec, id, s, k, fox, foy, plain);
             }
         }
         __syncthreads();
@@ -420,7 +426,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
         for (int c = (cnt - 1) & ~31; c >= 0; c -= 32) {
             const int jl = c + lane;
             unsigned m = __ballot_sync(0xffffffffu, jl < cnt && rel0 + jl < wlast &&
-                                                        cull_hit<BATCH>(s, jl, cxb, cyb));
+                                                        cull_hit(s, jl, cxb, cyb));
             while (m) {
                 const int bit = 31 - __clz(m);
                 m &= ~(1u << bit);
@@ -429,7 +435,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 Eval ev;
                 ev.G = -1.0f;
                 const bool cand = inside && pos < last;
-                const bool contrib = cand && eval_alpha<BATCH>(fpx, fpy, s, k, ev);
+                const bool contrib = cand && eval_alpha(fpx, fpy, s, k, ev);
                 if (COUNT) { c_visit += cand; c_full += (cand && ev.G >= 0.0f); c_contrib += contrib; }
                 // set in full by contributing lanes only; other lanes' values are never read
                 // (the fold below selects zero for them)
@@ -444,11 +450,9 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                     const float Ti = T * rinv;
                     const float w = ev.a * Ti;
                     gr[9] = w * g0_; gr[10] = w * g1_; gr[11] = w * g2_;
-                    float dLda = Ti * ((g2.z - S0) * g0_ + (g2.w - S1) * g1_ + (cb - S2) * g2_);
-                    dLda -= TfB * rinv;
-                    S0 = ev.a * g2.z + one_m_a * S0;
-                    S1 = ev.a * g2.w + one_m_a * S1;
-                    S2 = ev.a * cb + one_m_a * S2;
+                    const float cg = g2.z * g0_ + g2.w * g1_ + cb * g2_;
+                    const float dLda = Ti * (cg - Sg) - TfB * rinv;
+                    Sg = ev.a * cg + one_m_a * Sg;
                     T = Ti;
                     if (!ev.clamped) {
                         const float dA = dLda * ev.G;
@@ -459,7 +463,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                             gr[7] = dA * ev.P;
                             gr[8] = dA - gr[7];
                         }
-                        const float dpow = dLda * ev.A * ev.G;
+                        const float dpow = dLda * ev.a;           // a = A G when not clamped
                         const float dx = ev.dx, dy = ev.dy;
                         gr[2] = -0.5f * dpow * dx * dx;
                         gr[3] = -dpow * dx * dy;
@@ -468,10 +472,11 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                         const float sc = dpow * kInvUScale2;
                         gr[0] = sc * (g0.z * ev.s1);
                         gr[1] = sc * (g0.w * ev.s1 + g1.x * ev.s2);
-                        gr[5] = gr[6] = 0.0f;
-                        if (!plain && fabsf(g1.z) + fabsf(g1.w) < kStepDetect) {
-                            // d P / d(w'.d) = exp(-(w'.d)^2) / sqrt(pi); staged w' carries sqrt(log2 e)
-                            const float dz = dA * g2.y * ev.e * kInvSqrtPi;
+                        if (plain) {
+                            gr[5] = gr[6] = 0.0f;
+                        } else {
+                            // staged w' carries sqrt(log2 e); dzk is zero for step-mode splats
+                            const float dz = dA * (ev.e * s.dzk[k]);
                             const float dzs = dz * kInvSqrtLog2e;
                             gr[5] = dz * dx;
                             gr[6] = dz * dy;
@@ -522,7 +527,7 @@ template <int TW, int TH, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / kSplit<true, TW, TH>, (kMinBlocks<TW * TH / kSplit<true, TW, TH>, 5>))
     k_render_fwd(RenderLaunch p) {
     constexpr int SPLIT = kSplit<true, TW, TH>;
-    __shared__ Batch<BATCH> s;
+    __shared__ Batch<BATCH, false> s;
     if (!p.cfg.persistent) {
         render_tile_fwd<TW, TH, BATCH, COUNT>(p, blockIdx.x / SPLIT, blockIdx.x % SPLIT, s);
         return;
@@ -544,7 +549,7 @@ template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
 __global__ void __launch_bounds__(TW *TH / kSplit<false, TW, TH>, (kMinBlocks<TW * TH / kSplit<false, TW, TH>, 4>))
     k_render_bwd(RenderLaunch p) {
     constexpr int SPLIT = kSplit<false, TW, TH>;
-    __shared__ Batch<BATCH> s;
+    __shared__ Batch<BATCH, true> s;
     __shared__ uint32_t s_maxlast;
     if (!p.cfg.persistent) {
         render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, blockIdx.x / SPLIT, blockIdx.x % SPLIT, s, s_maxlast);
