@@ -36,7 +36,8 @@ class OrCamera(ctypes.Structure):
 
 class OrOpts(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("sh_degree", c_int),
-                ("fov_clamp", c_int), ("plain", c_int), ("rect_mode", c_int), ("lowpass", c_double)]
+                ("fov_clamp", c_int), ("plain", c_int), ("rect_mode", c_int), ("mip", c_int),
+                ("lowpass", c_double)]
 
 
 _LIB = None
@@ -51,7 +52,7 @@ def lib():
         L.or_abi_version.restype = c_int
         L.or_num_threads.restype = c_int
         L.or_project.argtypes = [c_int, dp, dp, dp, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts),
-                                 ip, fp, fp, ip, ip, fp, fp, dp, dp, dp, dp, dp]
+                                 ip, fp, fp, ip, ip, fp, fp, dp, dp, dp, dp, dp, dp]
         L.or_bin.argtypes = [c_int, ip, ip, fp, c_int, c_int, POINTER(c_ubyte), c_long,
                              POINTER(c_uint64), POINTER(c_uint32), POINTER(c_uint32),
                              POINTER(c_long)]
@@ -98,9 +99,11 @@ def make_camera(cam) -> OrCamera:
     return c
 
 
-def make_opts(tile=(16, 16), sh_degree=0, lowpass=0.3, plain=False, fov_clamp=True, rect_mode=0) -> OrOpts:
+def make_opts(tile=(16, 16), sh_degree=0, lowpass=0.3, plain=False, fov_clamp=True, rect_mode=0,
+              mip=False) -> OrOpts:
     o = OrOpts()
     o.rect_mode = int(rect_mode)
+    o.mip = 1 if mip else 0
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     o.sh_degree = int(sh_degree)
     o.fov_clamp = 1 if fov_clamp else 0
@@ -123,27 +126,29 @@ def grid(cam, tile):
     return tx, ty
 
 
-def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0):
+def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0, mip=False):
     """Per-splat projection (Eq. 2-5, 7-8; SH colour), plus canonical binning fields.
-    rect_mode 0: the 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4)."""
+    rect_mode 0: the 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4).
+    mip: the low-pass as Mip-Splatting's mass-preserving 2D filter; "opac1"/"opac2" are
+    then the compensated opacities the compositing uses ("comp" holds the factor)."""
     s = _scene64(sc)
     n = s["means"].shape[0]
-    o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp, rect_mode)
+    o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp, rect_mode, mip)
     c = make_camera(cam)
     out = dict(mode=np.zeros(n, np.int32), depth=np.zeros(n, np.float32),
                radius=np.zeros(n, np.float32), rect=np.zeros((n, 4), np.int32),
                tiles=np.zeros(n, np.int32), canon_abc=np.zeros((n, 3), np.float32),
                canon_mu=np.zeros((n, 2), np.float32), mu2=np.zeros((n, 2)),
                conic=np.zeros((n, 3)), wp=np.zeros((n, 2)), rgb=np.zeros((n, 3)),
-               var_terms=np.zeros((n, 2)))
+               var_terms=np.zeros((n, 2)), comp=np.ones(n))
     fp, dp, ip = c_float, c_double, c_int
     lib().or_project(n, _p(s["means"], dp), _p(s["scales"], dp), _p(s["quats"], dp),
                      _p(s["normals"], dp), _p(s["sh"], dp), _p(s["opac1"], dp), _p(s["opac2"], dp),
                      ctypes.byref(c), ctypes.byref(o), _p(out["mode"], ip), _p(out["depth"], fp), _p(out["radius"], fp),
                      _p(out["rect"], ip), _p(out["tiles"], ip), _p(out["canon_abc"], fp),
                      _p(out["canon_mu"], fp), _p(out["mu2"], dp), _p(out["conic"], dp),
-                     _p(out["wp"], dp), _p(out["rgb"], dp), _p(out["var_terms"], dp))
-    out["opac1"], out["opac2"] = s["opac1"], s["opac2"]
+                     _p(out["wp"], dp), _p(out["rgb"], dp), _p(out["var_terms"], dp), _p(out["comp"], dp))
+    out["opac1"], out["opac2"] = s["opac1"] * out["comp"], s["opac2"] * out["comp"]
     return out
 
 
@@ -176,7 +181,7 @@ def bin_pairs(proj, cam, tile=(16, 16), tile_mask=None):
 
 
 def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, tile_mask=None,
-           proj=None, bins=None, rect_mode=0):
+           proj=None, bins=None, rect_mode=0, mip=False):
     """Forward image: front-to-back compositing of the Eq. 10 pair weights over each
     tile's depth-sorted list (3-sigma tile culling, 1/255 floor, 0.99 clamp, 1e-4 stop).
 
@@ -184,7 +189,7 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     into margin_a for the 1/255 floor and margin_T for the 1e-4 stop, with n_comp the
     number of composited splats) and the projection/binning intermediates."""
     if proj is None:
-        proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode)
+        proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     W, H = int(cam.width), int(cam.height)
@@ -216,12 +221,12 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
 
 
 def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
-                  tile_mask=None, proj=None, bins=None):
+                  tile_mask=None, proj=None, bins=None, mip=False):
     """FP64 adjoint of the compositing alone (Eq. 10 blending, back to front) for the
     loss L = sum(dL_dimage * image): the per-splat screen-space gradients grad2d
-    [N,12] (fields G2D_FIELDS)."""
+    [N,12] (fields G2D_FIELDS; alpha1/alpha2 are the opacities the compositing used)."""
     if proj is None:
-        proj = project(sc, cam, tile, lowpass, fov_clamp)
+        proj = project(sc, cam, tile, lowpass, fov_clamp, mip=mip)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     n = int(np.asarray(proj["mode"]).shape[0])
@@ -245,27 +250,27 @@ def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, f
 
 
 def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
-               tile_mask=None, proj=None, bins=None):
+               tile_mask=None, proj=None, bins=None, mip=False, rect_mode=0):
     """FP64 adjoint of `render` for the loss L = sum(dL_dimage * image).
 
     Returns the parameter gradients and the per-splat screen-space gradients
     grad2d [N,12] (fields G2D_FIELDS)."""
     if proj is None:
-        proj = project(sc, cam, tile, lowpass, fov_clamp)
+        proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     g2 = rasterize_bwd(sc, cam, dL_dimage, tile, lowpass, plain, fov_clamp, tile_mask, proj, bins)
-    grads = project_bwd(sc, cam, proj["mode"], g2, tile, lowpass, fov_clamp)
+    grads = project_bwd(sc, cam, proj["mode"], g2, tile, lowpass, fov_clamp, mip)
     grads["grad2d"] = g2
     return grads
 
 
-def project_bwd(sc, cam, mode, grad2d, tile=(16, 16), lowpass=0.3, fov_clamp=True):
-    """FP64 adjoint of the projection (Eq. 2-5, 7-8, SH colour) for given screen-space
-    gradients grad2d [N,12]."""
+def project_bwd(sc, cam, mode, grad2d, tile=(16, 16), lowpass=0.3, fov_clamp=True, mip=False):
+    """FP64 adjoint of the projection (Eq. 2-5, 7-8, SH colour; with mip, the opacity
+    compensation) for given screen-space gradients grad2d [N,12]."""
     s = _scene64(sc)
     n = s["means"].shape[0]
-    o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp)
+    o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp, mip=mip)
     c = make_camera(cam)
     g = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
              normals=np.zeros((n, 3)), opac1=np.zeros(n), opac2=np.zeros(n),

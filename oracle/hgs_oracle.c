@@ -51,6 +51,8 @@ typedef struct {
     int fov_clamp;   /* 1: clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS convention) */
     int plain;       /* 1: plain 3D-GS, alpha = alpha1 * hat G (P unused)           */
     int rect_mode;   /* 0: 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4) */
+    int mip;         /* 1: the low-pass is a mass-preserving 2D filter (Mip-Splatting-HGS):
+                        both opacities scale by sqrt(det hat Sigma_0 / det hat Sigma)   */
     double lowpass;  /* l added to the diagonal of hat Sigma (3D-GS uses 0.3)        */
 } or_opts;
 
@@ -60,7 +62,7 @@ enum { OR_CULLED = 0, OR_NORMAL = 1, OR_STEP = 2, OR_HALF = 3 };
 #define OR_ALPHA_MAX 0.99
 #define OR_T_MIN 1e-4
 
-int or_abi_version(void) { return 4; }
+int or_abi_version(void) { return 5; }
 
 int or_num_threads(void)
 {
@@ -365,6 +367,8 @@ typedef struct {
     double uxc, uyc;
     double J00, J02, J11, J12;
     double M[2][3];
+    double S0[3];           /* M Sigma^w M^T (before the low-pass) */
+    double det0, comp;      /* its determinant; opacity factor (1 unless mip) */
     double S2[3];           /* hat Sigma a, b, c  */
     double det, Q[3];       /* conic A, B, C      */
     double mu2[2];
@@ -437,6 +441,14 @@ static void project_fp64(const double *mean, const double *scale, const double *
     f->S2[0] = S00 + o->lowpass; f->S2[1] = S01; f->S2[2] = S11 + o->lowpass;
     f->det = f->S2[0] * f->S2[2] - f->S2[1] * f->S2[1];
     f->Q[0] = f->S2[2] / f->det; f->Q[1] = -f->S2[1] / f->det; f->Q[2] = f->S2[0] / f->det;
+    /* Mip-Splatting's 2D filter: convolving alpha hat G_0 with the normalised N(0, l I)
+       gives sqrt(det hat Sigma_0 / det hat Sigma) alpha hat G, the same total mass; by
+       the reading of the low-pass on the half-footprint (total probability) the
+       half-Gaussian weight carries the same factor on both opacities. */
+    f->S0[0] = S00; f->S0[1] = S01; f->S0[2] = S11;
+    f->det0 = S00 * S11 - S01 * S01;
+    f->comp = 1.0;
+    if (o->mip) f->comp = f->det0 > 0 ? sqrt(f->det0 / f->det) : 0.0;
 
     /* projected centre */
     f->mu2[0] = cam->fx * f->t[0] / tz + cam->cx;
@@ -504,7 +516,7 @@ int or_project(int n, const double *means, const double *scales, const double *q
                const or_camera *cam, const or_opts *o,
                int *mode, float *depth, float *radius, int *rect, int *tiles,
                float *canon_abc, float *canon_mu,
-               double *mu2, double *conic, double *wp, double *rgb, double *var_terms)
+               double *mu2, double *conic, double *wp, double *rgb, double *var_terms, double *comp)
 {
     int nc = (o->sh_degree + 1) * (o->sh_degree + 1);
 #pragma omp parallel for schedule(static)
@@ -532,6 +544,7 @@ int or_project(int n, const double *means, const double *scales, const double *q
         if (f.mode == OR_STEP) { wp[2 * i] = f.w[0]; wp[2 * i + 1] = f.w[1]; }
         for (int j = 0; j < 3; ++j) rgb[3 * i + j] = f.rgb[j];
         if (var_terms) { var_terms[2 * i] = f.var_s; var_terms[2 * i + 1] = f.v; }
+        if (comp) comp[i] = f.comp;
     }
     return 0;
 }
@@ -871,7 +884,6 @@ int or_project_bwd(int n, const double *means, const double *scales, const doubl
                    double *g_means, double *g_scales, double *g_quats, double *g_normals,
                    double *g_op1, double *g_op2, double *g_sh)
 {
-    (void)op1; (void)op2;
     int nc = (o->sh_degree + 1) * (o->sh_degree + 1);
     const double *V = cam->viewmat;
     double Rc[3][3] = {{V[0], V[1], V[2]}, {V[4], V[5], V[6]}, {V[8], V[9], V[10]}};
@@ -883,8 +895,10 @@ int or_project_bwd(int n, const double *means, const double *scales, const doubl
         const double *shi = sh + 3 * nc * i;
         project_fp64(means + 3 * i, scales + 3 * i, quats + 4 * i, normals + 3 * i, shi,
                      o->sh_degree, cam, o, &f);
-        g_op1[i] += gg[7];
-        g_op2[i] += gg[8];
+        /* grad2d[7..8] are taken w.r.t. the opacities the compositing used, comp * op */
+        g_op1[i] += f.comp * gg[7];
+        g_op2[i] += f.comp * gg[8];
+        const double g_comp = op1[i] * gg[7] + op2[i] * gg[8];
 
         double g_mean[3] = {0, 0, 0};
         /* colour: rgb = max(0, sum sh*Y(dir) + 1/2), dir = (mu - campos)/|mu - campos| */
@@ -944,6 +958,14 @@ int or_project_bwd(int n, const double *means, const double *scales, const doubl
             for (int b = 0; b < 2; ++b) T1[a][b] = Qm[a][0] * GQm[0][b] + Qm[a][1] * GQm[1][b];
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) Gs[a][b] = -(T1[a][0] * Qm[0][b] + T1[a][1] * Qm[1][b]);
+        /* mip: comp = sqrt(det S0 / det(S0 + l I)),
+           d comp = comp/2 tr((S0^-1 - hat Sigma^-1) dS0), and d hat Sigma = dS0 */
+        if (o->mip && f.det0 > 0) {
+            const double h = 0.5 * g_comp * f.comp;
+            const double I0[2][2] = {{f.S0[2] / f.det0, -f.S0[1] / f.det0}, {-f.S0[1] / f.det0, f.S0[0] / f.det0}};
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) Gs[a][b] += h * (I0[a][b] - Qm[a][b]);
+        }
         /* hat Sigma = M Sigma^w M^T + l I:  gM += 2 Gs M Sw,  gSw += M^T Gs M */
         double MSw[2][3];
         for (int a = 0; a < 2; ++a)

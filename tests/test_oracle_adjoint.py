@@ -55,10 +55,13 @@ def _loss(sc, cam, g, **kw):
     return float(np.sum(oracle.render(sc, cam, **kw)["image"] * g))
 
 
-@pytest.mark.parametrize("seed,plain", [(0, False), (1, False), (2, True)])
-def test_adjoint_matches_central_differences(seed, plain):
+@pytest.mark.parametrize("seed,plain,mip", [(0, False, False), (1, False, False), (2, True, False),
+                                             (3, False, True)])
+def test_adjoint_matches_central_differences(seed, plain, mip):
+    """mip: the opacity compensation of the Mip-Splatting 2D filter, with its gradient
+    through det hat Sigma_0 / det hat Sigma into the geometry."""
     sc, cam, g = _scene(seed)
-    kw = dict(tile=(16, 16), plain=plain)
+    kw = dict(tile=(16, 16), plain=plain, mip=mip)
     out = oracle.render(sc, cam, **kw)
     # both clamp branches of the Jacobian are exercised: splats 0 and 1 have their
     # centre beyond 1.3 tan(fov/2) and still cover tiles
