@@ -252,6 +252,7 @@ def run_gpu(args):
     }
     if args.rect_modes:
         result["rect_mode_1"] = run_rect_mode1(args, dev, g, dL, rast, n_pairs)
+        result["mip"] = run_mip(args, dev, g, dL, rast)
     if args.sweep:
         result["sweep"] = run_sweep(args, dev)
     if args.multiview:
@@ -578,18 +579,16 @@ def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_00
     return out
 
 
-def run_rect_mode1(args, dev, g, dL, rast0, pairs0):
-    """The same step with the per-half valid regions of Sec. 3.4 as tile rectangles
-    (hgs_config.rect_mode = 1): time, pair count, and the PSNR of its image against the
-    3-sigma-square image of the main run (the two rules differ where a splat reaches
-    beyond its 3-sigma ellipse)."""
+def _run_variant(args, dev, g, dL, rast0, label, **cfg_kw):
+    """The main step under another hgs_config option: graph-replay time, pair count and
+    the PSNR of its image against the main run's image."""
     import torch
     from paper_2406_02720_b300 import hgs as H
     from paper_2406_02720_b300.multiview import time_replays
     from paper_2406_02720_b300.rasterizer import Gaussians, GraphStep, Rasterizer
     img0 = rast0.images()[0].clone()
     sc, cams, _ = _scene(args)
-    cfg = H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch, persistent=args.persistent, rect_mode=1)
+    cfg = H.make_config(tile=(args.tile_w, args.tile_h), batch=args.batch, persistent=args.persistent, **cfg_kw)
     r = Rasterizer(cams, sc.n, cfg, device=dev)
     r.forward(g)
     pairs = int(r.num_pairs.item())
@@ -597,14 +596,31 @@ def run_rect_mode1(args, dev, g, dL, rast0, pairs0):
     step = GraphStep(r, g, dL, Gaussians.empty_like(g))
     ms = time_replays(step, args.sweep_steps * 5)
     if r.read_status():
-        raise RuntimeError("device status in the rect_mode 1 step")
+        raise RuntimeError(f"device status in the {label} step")
     r.forward(g)
     mse = float(torch.mean((r.images()[0] - img0) ** 2).item())
     pix = cams[0].width * cams[0].height
     del step, r
     torch.cuda.empty_cache()
-    return {"ms_per_step": ms, "Mpixel_per_s": pix / (ms * 1e3), "pairs": pairs, "pairs_rect_mode_0": pairs0,
-            "psnr_vs_rect_mode_0_db": 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")}
+    return ms, pix / (ms * 1e3), pairs, (10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf"))
+
+
+def run_rect_mode1(args, dev, g, dL, rast0, pairs0):
+    """The same step with the per-half valid regions of Sec. 3.4 as tile rectangles
+    (hgs_config.rect_mode = 1): time, pair count, and the PSNR of its image against the
+    3-sigma-square image of the main run (the two rules differ where a splat reaches
+    beyond its 3-sigma ellipse)."""
+    ms, mpix, pairs, psnr = _run_variant(args, dev, g, dL, rast0, "rect_mode 1", rect_mode=1)
+    return {"ms_per_step": ms, "Mpixel_per_s": mpix, "pairs": pairs, "pairs_rect_mode_0": pairs0,
+            "psnr_vs_rect_mode_0_db": psnr}
+
+
+def run_mip(args, dev, g, dL, rast0):
+    """The same step as Mip-Splatting-HGS (hgs_config.mip = 1: the low-pass as a
+    normalised 2D filter, opacities scaled per (view, splat)): time, and the PSNR of its
+    image against the main run's (the compensation darkens splats of pixel size)."""
+    ms, mpix, pairs, psnr = _run_variant(args, dev, g, dL, rast0, "mip", mip=True)
+    return {"ms_per_step": ms, "Mpixel_per_s": mpix, "pairs": pairs, "psnr_vs_default_db": psnr}
 
 
 # ---- CPU oracle (reported baseline / reference arm) -----------------------------------------
@@ -627,15 +643,44 @@ class OracleSample:
         self.splat_order = self.rng.permutation(self.sc.n)
         self.pr_full = oracle.project(self.sc, self.cam, self.tile)
         self.g2_sub = None
+        # pairs per tile from the rectangles (a 2-D difference array), to stratify the
+        # sampled tiles by list length
+        r = self.pr_full["rect"][self.pr_full["tiles"] > 0].astype(np.int64)
+        d = np.zeros((ty + 1, tx + 1), np.int64)
+        np.add.at(d, (r[:, 1], r[:, 0]), 1)
+        np.add.at(d, (r[:, 1], r[:, 2]), -1)
+        np.add.at(d, (r[:, 3], r[:, 0]), -1)
+        np.add.at(d, (r[:, 3], r[:, 2]), 1)
+        self.tile_pairs = np.cumsum(np.cumsum(d, 0), 1)[:ty, :tx].reshape(-1)
+        self.by_pairs = np.argsort(self.tile_pairs, kind="stable")
+        # the per-call cost of the compositing calls that does not depend on the tiles
+        # (full-image buffers): measured once with no tile selected, not scaled
+        self.t_fixed = statistics.median(self._composite(np.zeros(self.n_tiles, np.uint8)) for _ in range(3))
 
-    def step(self, m, k):
-        """Runs the sample; returns (estimated full-step seconds, measured seconds)."""
+    def tiles_for(self, k, u=0.5):
+        """k tiles, one from each of k equal strata of the tiles ordered by list length
+        (systematic sampling at offset u in [0, 1)): each stands for n_tiles / k tiles
+        of like cost."""
+        pos = ((np.arange(k) + u) * self.n_tiles / k).astype(np.int64)
+        return self.by_pairs[np.minimum(pos, self.n_tiles - 1)]
+
+    def _composite(self, mask):
+        o = self.oracle
+        bins = o.bin_pairs(self.pr_full, self.cam, self.tile, tile_mask=mask)
+        t0 = time.perf_counter()
+        o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
+        o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
+        return time.perf_counter() - t0
+
+    def step(self, m, k, u=0.5):
+        """Runs the sample (tile strata at offset u); returns (estimated full-step
+        seconds, measured seconds)."""
         o = self.oracle
         m = max(1, min(m, self.sc.n))
         k = max(1, min(k, self.n_tiles))
         sub = self.sc.subset(np.sort(self.splat_order[:m]))
         mask = np.zeros(self.n_tiles, np.uint8)
-        mask[self.tile_order[:k]] = 1
+        mask[self.tiles_for(k, u)] = 1
         g2 = np.random.default_rng(m).normal(size=(m, 12))
         # the sampled tiles' lists (binning is timed on the splat subset above)
         tb = time.perf_counter()
@@ -652,14 +697,15 @@ class OracleSample:
         o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
         t4 = time.perf_counter()
         per_splat = (t3 - t0) * self.sc.n / m
-        per_tile = (t4 - t3) * self.n_tiles / k
+        per_tile = self.t_fixed + max(t4 - t3 - self.t_fixed, 0.0) * self.n_tiles / k
         del out
         return per_splat + per_tile, t4 - t0 + prep
 
     def describe(self, m, k):
         return (f"projection, binning and projection adjoint of {m} of {self.sc.n} splats (seeded subset, "
-                f"scaled by n/m); compositing fwd+bwd of {k} of {self.n_tiles} tiles (seeded, scaled by the "
-                "tile fraction); FP64")
+                f"scaled by n/m); compositing fwd+bwd of {k} of {self.n_tiles} tiles (one per stratum of "
+                "the tiles ordered by list length; the time beyond the calls' fixed cost scaled by the tile "
+                "fraction); FP64")
 
 
 def cpu_baseline(args, m=None, k=48):
@@ -689,8 +735,10 @@ def run_reference(args):
         m = int(min(samp.sc.n, max(2_000, m * scale)))
         k = int(min(samp.n_tiles, max(1, k * scale)))
     vals = []
-    for _ in range(args.steps):
-        est, _ = samp.step(m, k)
+    for i in range(args.steps):
+        # the strata offset moves every step, so that the steps together sample
+        # steps x k different tiles; the mean of their estimates is the reported step
+        est, _ = samp.step(m, k, (i + 0.5) / args.steps)
         vals.append(est)
     est = statistics.mean(vals)
     pixels = samp.cam.width * samp.cam.height
@@ -726,7 +774,8 @@ def main(argv=None):
     ap.add_argument("--mv-steps", type=int, default=10)
     ap.add_argument("--sweep", action="store_true", help="also time the stress sweep (100k..6M splats)")
     ap.add_argument("--no-rect-modes", dest="rect_modes", action="store_false",
-                    help="skip the step with per-half tile rectangles (rect_mode 1)")
+                    help="skip the steps with per-half tile rectangles (rect_mode 1) and with the "
+                         "Mip-Splatting 2D filter (mip)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)

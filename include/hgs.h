@@ -119,7 +119,18 @@ typedef struct {
  *                    half's outer surface faces that way, the splitting plane's
  *                    cut ellipse elsewhere; low-pass added in quadrature); a splat
  *                    with both halves below 1/255 is culled.  Mode 1 changes the
- *                    image where a splat reached beyond its 3-sigma ellipse. */
+ *                    image where a splat reached beyond its 3-sigma ellipse.
+ *   mip            : 1 = Mip-Splatting-HGS: the low-pass is Mip-Splatting's 2D
+ *                    filter, a normalised convolution with N(0, lowpass I) rather
+ *                    than a dilation, so both opacities are scaled by
+ *                    sqrt(det hat Sigma_0 / det hat Sigma) per (view, splat) (hat
+ *                    Sigma_0: before the low-pass).  The records then hold the
+ *                    scaled opacities and grad2d[7..8] is taken w.r.t. them;
+ *                    hgs_project_bwd carries the factor into the parameters.
+ *                    Mip-Splatting's 3D filter needs no kernel: it is the scales
+ *                    sqrt(s^2 + s_f^2) and opacities scaled by prod s / prod
+ *                    sqrt(s^2 + s_f^2), applied by the caller.  The rect_mode 1
+ *                    opacity test uses the unscaled opacities (a superset). */
 typedef struct {
     int tile_w, tile_h;
     int batch;
@@ -129,6 +140,7 @@ typedef struct {
     int persistent;
     int accumulate;
     int rect_mode;
+    int mip;
 } hgs_config;
 
 /* Per-(view, splat) projected records written by hgs_project, [n_views*n] rows.

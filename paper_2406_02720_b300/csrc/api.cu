@@ -37,7 +37,8 @@ bool cfg_ok(const hgs_config *c) {
     const bool batch = c->batch == 0 || c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256 ||
                        c->batch == 512;
     const bool rect = c->rect_mode == 0 || c->rect_mode == 1;
-    return shape && batch && rect && isfinite(c->lowpass) && c->lowpass >= 0.0f;
+    const bool mip = c->mip == 0 || c->mip == 1;
+    return shape && batch && rect && mip && isfinite(c->lowpass) && c->lowpass >= 0.0f;
 }
 
 hgs_status build_views(const hgs_camera *cams, int nv, const hgs_config *cfg, ViewTable *vt) {

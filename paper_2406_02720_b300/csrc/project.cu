@@ -304,6 +304,7 @@ struct Proj {
     T qn, qh[4], R[3][3], L[3][3], t[3], uxc, uyc;
     bool clx, cly;
     T J00, J02, J11, J12, M[2][3], P[2][3], a, b, c, det, Q[3];
+    T n0, n1, det0;          // hat Sigma_0 = P P^T (before the low-pass): diagonal, determinant
     T nn, nh[3], u[3], var_s, k[2], w[2], v;
     int mode;
 
@@ -347,14 +348,15 @@ struct Proj {
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int kk = 0; kk < 3; ++kk) P[i][kk] = M[i][0] * L[0][kk] + M[i][1] * L[1][kk] + M[i][2] * L[2][kk];
-        const T n0 = P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2];
-        const T n1 = P[1][0] * P[1][0] + P[1][1] * P[1][1] + P[1][2] * P[1][2];
+        n0 = P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2];
+        n1 = P[1][0] * P[1][0] + P[1][1] * P[1][1] + P[1][2] * P[1][2];
         a = n0 + (T)lp;
         b = P[0][0] * P[1][0] + P[0][1] * P[1][1] + P[0][2] * P[1][2];
         c = n1 + (T)lp;
         T cr[3];
         cross3(P[0], P[1], cr);
-        det = dot3(cr, cr) + (T)lp * (n0 + n1) + (T)lp * (T)lp;
+        det0 = dot3(cr, cr);
+        det = det0 + (T)lp * (n0 + n1) + (T)lp * (T)lp;
         T id = (T)1 / det;
         Q[0] = c * id; Q[1] = -b * id; Q[2] = a * id;
         nn = sqrt((T)nrm[0] * nrm[0] + (T)nrm[1] * nrm[1] + (T)nrm[2] * nrm[2]);
@@ -382,6 +384,9 @@ struct Proj {
     __device__ __forceinline__ bool degenerate() const {
         return mode == MODE_NORMAL && v < (T)kVRelFp64 * var_s;
     }
+
+    // Opacity factor of the Mip-Splatting 2D filter: sqrt(det hat Sigma_0 / det hat Sigma).
+    __device__ __forceinline__ T mip_factor() const { return det0 > (T)0 ? sqrt(det0 / det) : (T)0; }
 };
 
 // ---- real spherical harmonics, degree <= 3 ---------------------------------
@@ -640,6 +645,7 @@ __device__ __forceinline__ HalfPlane half_plane_fp64(const Params &P, const hgs_
 // half-plane terms kept for the record.  False when the splat is not drawn.
 struct Geo {
     float u11, u12, u22, wpx, wpy;
+    float comp;              // opacity factor: 1, or the Mip-Splatting 2D filter's
 };
 
 __device__ __forceinline__ bool project_geo(const ProjLaunch &p, const Params &P, float o1, float o2, int v,
@@ -659,9 +665,13 @@ __device__ __forceinline__ bool project_geo(const ProjLaunch &p, const Params &P
     const float n0 = dot3(cb.P[0], cb.P[0]), n1 = dot3(cb.P[1], cb.P[1]);
     float cr[3];
     cross3(cb.P[0], cb.P[1], cr);
-    const float det = dot3(cr, cr) + lp * (n0 + n1) + lp * lp;
+    const float det0 = dot3(cr, cr);
+    const float det = det0 + lp * (n0 + n1) + lp * lp;
     const float a_ = cb.a, b_ = cb.b, c_ = cb.c;
     out.wpx = out.wpy = 0.0f;
+    // Mip-Splatting's 2D filter: the low-pass as a normalised convolution scales the
+    // footprint by sqrt(det hat Sigma_0 / det hat Sigma), both halves alike
+    out.comp = p.cfg.mip ? sqrtf(det0 / det) : 1.0f;
     const float nn = sqrtf(dot3(P.n, P.n));
     if (nn >= 1e-12f) {
         const float in = 1.0f / nn;
@@ -713,7 +723,7 @@ __device__ __forceinline__ void project_record(const ProjLaunch &p, const StageS
     float4 *rec = reinterpret_cast<float4 *>(p.out.rec) + 4 * vi;
     rec[0] = make_float4(ctr[0], ctr[1], ctr[2], ctr[3]);
     rec[1] = make_float4(g.u11, g.u12, g.u22, g.wpx);
-    rec[2] = make_float4(g.wpy, o1, o2, fmaxf(rgb[0], 0.0f));
+    rec[2] = make_float4(g.wpy, o1 * g.comp, o2 * g.comp, fmaxf(rgb[0], 0.0f));
     rec[3] = make_float4(fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), 0.0f, 0.0f);
 }
 
@@ -776,9 +786,10 @@ struct G2 {
 };
 
 template <typename T>
+// g_comp: dL/d(opacity factor) of the Mip-Splatting 2D filter (0 without it).
 __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const hgs_camera &cam,
                                          const float *g2, float gm[3], float gs[3], float gq[4],
-                                         float gn[3]) {
+                                         float gn[3], T g_comp = 0) {
     const float *V = cam.viewmat;
     T gA = g2[2], gB = g2[3], gC = g2[4];
     T gk[2] = {0, 0}, gvar = 0;
@@ -800,6 +811,14 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
     T Gs00 = -(X00 * f.Q[0] + X01 * f.Q[1]);
     T Gs01 = -(X00 * f.Q[1] + X01 * f.Q[2]);
     T Gs11 = -(X10 * f.Q[1] + X11 * f.Q[2]);
+    // comp = sqrt(det hat Sigma_0 / det hat Sigma):
+    // d comp = comp/2 tr((hat Sigma_0^-1 - hat Sigma^-1) d hat Sigma_0), d hat Sigma = d hat Sigma_0
+    if (g_comp != (T)0 && f.det0 > (T)0) {
+        const T h = (T)0.5 * g_comp * f.mip_factor(), i0 = (T)1 / f.det0;
+        Gs00 += h * (f.n1 * i0 - f.Q[0]);
+        Gs01 += h * (-f.b * i0 - f.Q[1]);
+        Gs11 += h * (f.n0 * i0 - f.Q[2]);
+    }
     // hat Sigma = P P^T + l I and k = P u
     T gP[2][3], gu[3];
 #pragma unroll
@@ -880,7 +899,7 @@ struct Grads {
 
 // FP64 adjoint of the projection of one near-degenerate splat.
 __device__ __forceinline__ Grads proj_vjp_fp64(const Params &P, const hgs_camera &cam, float lp, int fov_clamp,
-                                               const G2 &g2) {
+                                               const G2 &g2, double g_comp) {
     Proj<double> d;
     d.run(P.m, P.s, P.q, P.n, cam, lp, fov_clamp);
     Grads r;
@@ -888,7 +907,7 @@ __device__ __forceinline__ Grads proj_vjp_fp64(const Params &P, const hgs_camera
     for (int k = 0; k < 3; ++k) r.m[k] = r.s[k] = r.n[k] = 0.0f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.q[k] = 0.0f;
-    proj_vjp<double>(d, P.s, cam, g2.v, r.m, r.s, r.q, r.n);
+    proj_vjp<double>(d, P.s, cam, g2.v, r.m, r.s, r.q, r.n, g_comp);
     return r;
 }
 
@@ -938,13 +957,17 @@ __global__ void __launch_bounds__(kProjBlock, 4) k_project_bwd(ProjBwdLaunch p) 
             for (int j = 0; j < 12; ++j) any |= (g2.v[j] != 0.0f);
             if (!any) continue;
             const hgs_camera &cam = p.cams[v];
-            go1 += g2.v[7];
-            go2 += g2.v[8];
             Proj<float> f;
             f.run(P.m, P.s, P.q, P.n, cam, lp, p.cfg.fov_clamp);
+            // grad2d[7..8] are w.r.t. the opacities the compositing used (x comp with mip)
+            const bool mip = p.cfg.mip != 0;
+            const float comp = mip ? f.mip_factor() : 1.0f;
+            go1 += comp * g2.v[7];
+            go2 += comp * g2.v[8];
+            const float g_comp = mip ? sm.o1[t] * g2.v[7] + sm.o2[t] * g2.v[8] : 0.0f;
             const bool defer = f.degenerate();     // geometry adjoint by k_project_bwd_fp64
             list_append(p.fp64_list, defer, (uint32_t)vi);
-            if (!defer) proj_vjp<float>(f, P.s, cam, g2.v, gm, gs, gq, gn);
+            if (!defer) proj_vjp<float>(f, P.s, cam, g2.v, gm, gs, gq, gn, g_comp);
             // SH colour: rgb = max(0, sum c Y(dir) + 1/2), dir = unit(mu - camera centre)
             float cpos[3];
             camera_centre(cam, cpos);
@@ -1043,7 +1066,8 @@ __global__ void __launch_bounds__(kProjBlock) k_project_bwd_fp64(ProjBwdLaunch p
             const float4 a = g4[j];
             g2.v[4 * j] = a.x; g2.v[4 * j + 1] = a.y; g2.v[4 * j + 2] = a.z; g2.v[4 * j + 3] = a.w;
         }
-        const Grads r = proj_vjp_fp64(P, p.cams[v], p.cfg.lowpass, p.cfg.fov_clamp, g2);
+        const double g_comp = p.cfg.mip ? (double)p.g.opac1[i] * g2.v[7] + (double)p.g.opac2[i] * g2.v[8] : 0.0;
+        const Grads r = proj_vjp_fp64(P, p.cams[v], p.cfg.lowpass, p.cfg.fov_clamp, g2, g_comp);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             atomicAdd(p.out.means + 3 * (size_t)i + k, r.m[k]);

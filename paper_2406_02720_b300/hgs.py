@@ -30,7 +30,7 @@ class HgsCamera(ctypes.Structure):
 class HgsConfig(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("batch", c_int), ("lowpass", c_float),
                 ("fov_clamp", c_int), ("plain", c_int), ("persistent", c_int), ("accumulate", c_int),
-                ("rect_mode", c_int)]
+                ("rect_mode", c_int), ("mip", c_int)]
 
 
 class HgsGaussians(ctypes.Structure):
@@ -203,7 +203,7 @@ STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd
 
 # ---- struct builders ----------------------------------------------------------------------
 def make_config(tile=(16, 16), batch=0, lowpass=0.3, fov_clamp=True, plain=False, persistent=True,
-                accumulate=False, rect_mode=0) -> HgsConfig:
+                accumulate=False, rect_mode=0, mip=False) -> HgsConfig:
     """hgs_config with this package's defaults: 16x16 tiles, per-direction batch,
     3D-GS low-pass and FOV clamp, half-Gaussian weights, and compositing as persistent
     blocks over the heaviest-first tile queue (faster than one block per tile even for
@@ -217,6 +217,7 @@ def make_config(tile=(16, 16), batch=0, lowpass=0.3, fov_clamp=True, plain=False
     c.persistent = 1 if persistent else 0
     c.accumulate = 1 if accumulate else 0
     c.rect_mode = int(rect_mode)
+    c.mip = 1 if mip else 0
     return c
 
 

@@ -26,12 +26,12 @@ EXEMPT_ATOL = 2e-2
 
 
 def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persistent=True,
-               pair_capacity=None, dL=None, rect_mode=0):
+               pair_capacity=None, dL=None, rect_mode=0, mip=False):
     import torch
     from paper_2406_02720_b300 import hgs as H
     from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
     cfg = H.make_config(tile=tile, batch=batch, lowpass=lowpass, plain=plain, persistent=persistent,
-                        rect_mode=rect_mode)
+                        rect_mode=rect_mode, mip=mip)
     g = Gaussians.from_scene(sc)
     r = Rasterizer(cams, sc.n, cfg, pair_capacity=pair_capacity, keep_keys=True)
     r.forward(g)

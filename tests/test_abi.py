@@ -40,6 +40,9 @@ def test_host_validation_rejects_bad_arguments():
     assert L.hgs_layout(cams, 1, ctypes.byref(bad_batch), None, None) == H.HGS_ERR_INVALID
     bad_rect = H.make_config(rect_mode=2)
     assert L.hgs_layout(cams, 1, ctypes.byref(bad_rect), None, None) == H.HGS_ERR_INVALID
+    bad_mip = H.make_config()
+    bad_mip.mip = 2
+    assert L.hgs_layout(cams, 1, ctypes.byref(bad_mip), None, None) == H.HGS_ERR_INVALID
     cfg = H.make_config()
     assert L.hgs_layout(cams, 0, ctypes.byref(cfg), None, None) == H.HGS_ERR_INVALID
     assert L.hgs_layout(cams, H.HGS_MAX_VIEWS + 1, ctypes.byref(cfg), None, None) == H.HGS_ERR_INVALID
@@ -83,6 +86,6 @@ def test_host_validation_rejects_bad_arguments():
 
 def test_camera_struct_layout_matches_header():
     assert ctypes.sizeof(H.HgsCamera) == 4 * (12 + 4 + 2 + 1 + 3)
-    assert ctypes.sizeof(H.HgsConfig) == 9 * 4
+    assert ctypes.sizeof(H.HgsConfig) == 10 * 4
     cams = H.make_cameras([scenes.config3_camera()])
     assert cams[0].width == 1920 and cams[0].viewmat[11] == np.float32(12.0)
