@@ -309,16 +309,20 @@ def alg_bytes(n, n_pairs, total_tiles):
 
 
 # Algorithmic operations per counted event of the compositing kernels, counted
-# from the source of eval_alpha / render_tile_fwd / render_tile_bwd (see DESIGN):
-#   visit  : offset, quadratic form, two cut-off compares              9 FP32
-#   full   : Eq. 8 via A&S 7.1.26, Eq. 10 mix, clamp, floor compare     20 FP32 + 3 MUFU
-#   comp   : transmittance update, stop test, colour accumulation       7 FP32
-#   contrib: backward adjoint of one composited pair                   58 FP32 + 2 MUFU
+# from the source of quad-form / weight evaluation and the two tile loops of render.cu
+# (FP32-pipe arithmetic and compares; selects and integer work not counted):
+#   visit  : pixel offset (2), quadratic form |U d|^2 (5), cut-off compare   8 FP32
+#   full   : w'.d (2), A&S 7.1.26 argument and polynomial (6), exp(-z^2)
+#            argument (1), erfc/2 (1), P (2), Eq. 10 mix (2), clamp and
+#            floor compares (2)                                              16 FP32 + 3 MUFU
+#   comp   : transmittance update and stop test (3), colour accumulation (4)  7 FP32
+#   contrib: backward adjoint of one composited pair (T rebuilt by division,
+#            colour-behind recurrence as one dot product, 12 gradients)     39 FP32 + 1 MUFU
 #   red    : fold of 12 gradients over lane pairs (one shuffle+add
 #            level, all 32 lanes) when more than 16 lanes contribute    384 FP32
-OPS = {"fwd": {"fp32": {"fwd_visit": 9, "fwd_full": 20, "fwd_comp": 7}, "mufu": {"fwd_full": 3}},
-       "bwd": {"fp32": {"bwd_visit": 9, "bwd_full": 20, "bwd_contrib": 58, "bwd_warp_red": 384},
-               "mufu": {"bwd_full": 3, "bwd_contrib": 2}}}
+OPS = {"fwd": {"fp32": {"fwd_visit": 8, "fwd_full": 16, "fwd_comp": 7}, "mufu": {"fwd_full": 3}},
+       "bwd": {"fp32": {"bwd_visit": 8, "bwd_full": 16, "bwd_contrib": 39, "bwd_warp_red": 384},
+               "mufu": {"bwd_full": 3, "bwd_contrib": 1}}}
 
 
 def alu_work(stats, key):
