@@ -170,13 +170,16 @@ def run_gpu(args):
             r.project_bwd(self.g, self.grads)
             evs[5].record()
 
+    # the timed step: the plain graph (the phase events of `step` cost ~10 us per replay,
+    # ~0.1 ms in the pipelined end-to-end loop); `step` only for the phase breakdown
     step = Step(rast, g, dL, grads)
+    plain_step = GraphStep(rast, g, dL, grads)
     torch.cuda.synchronize()
     st = rast.read_status()
     if st:
         raise RuntimeError(f"device status {st} after capture")
     for _ in range(args.warmup):
-        step.replay()
+        plain_step.replay()
     torch.cuda.synchronize()
 
     # ---- timed region: K back-to-back replays --------------------------------------------
@@ -189,7 +192,7 @@ def run_gpu(args):
     time.sleep(0.3)
     t0.record()
     for _ in range(args.steps):
-        step.replay()
+        plain_step.replay()
     t1.record()
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -229,8 +232,8 @@ def run_gpu(args):
     roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks)
 
     # ---- end to end through host buffers --------------------------------------------------
-    e2e = run_e2e(args, rast, g, dL, grads, step, pixels, dev)
-    e2e_full = run_e2e_params_over_pcie(args, rast, g, dL, grads, step, pixels, dev)
+    e2e = run_e2e(args, rast, g, dL, grads, pixels, dev)
+    e2e_full = run_e2e_params_over_pcie(args, rast, g, dL, grads, plain_step, pixels, dev)
 
     launches = launches_per_step(rast.total_tiles, persistent=bool(cfg.persistent))
     result = {
@@ -408,24 +411,41 @@ def phase_rooflines(phases, stats, n_pairs, n, total_tiles):
     return out
 
 
-def run_e2e(args, rast, g, dL, grads, step, pixels, dev):
+def run_e2e(args, rast, g, dL, grads, pixels, dev):
     """The step end to end through the public API, with each step's data crossing
     PCIe inside the timed region.  The splat parameters are the model's state and stay
     resident in HBM (as weights do in a training step); each step's inputs are its
     camera and the upstream image gradient dL/dimage, copied from pinned host memory,
-    and its result is the rendered image, copied back to pinned host memory.  Copies
-    run on two side streams, double-buffered, so step k+1's upload and step k's
-    download overlap step k's kernels."""
+    and its result is the rendered image, copied back to pinned host memory.  PCIe
+    copies run on two side streams, double-buffered, so step k+1's upload and step k's
+    download overlap step k's kernels; the on-device copies between the staging
+    buffers and the step's own buffers are captured into the step's graph (one graph
+    per staging buffer), so each step is one graph launch.  (Capturing them as graph
+    branches parallel to the kernels measured no faster.)"""
     import torch
+    from paper_2406_02720_b300.rasterizer import GraphStep
+
+    class StagedStep(GraphStep):
+        def __init__(self, src_dl, src_cam, dst_img):
+            self.src_dl, self.src_cam, self.dst_img = src_dl, src_cam, dst_img
+            super().__init__(rast, g, dL, grads)
+
+        def _body(self, backward):
+            self.dL.copy_(self.src_dl, non_blocking=True)
+            self.rast.cams_dev.copy_(self.src_cam, non_blocking=True)
+            super()._body(backward)
+            self.dst_img.copy_(self.rast.image, non_blocking=True)
+
     main = torch.cuda.current_stream(dev)
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     cam_bytes = rast.cams_dev.numel()
     host_dl = [dL.detach().cpu().pin_memory() for _ in range(2)]
     host_cam = [rast.cams_dev.detach().cpu().pin_memory() for _ in range(2)]
     host_img = [torch.empty(rast.image.shape, dtype=rast.image.dtype, pin_memory=True) for _ in range(2)]
-    stage_dl = [torch.empty_like(dL) for _ in range(2)]
-    stage_cam = [torch.empty_like(rast.cams_dev) for _ in range(2)]
+    stage_dl = [dL.detach().clone() for _ in range(2)]
+    stage_cam = [rast.cams_dev.detach().clone() for _ in range(2)]
     stage_img = [torch.empty_like(rast.image) for _ in range(2)]
+    steps = [StagedStep(stage_dl[b], stage_cam[b], stage_img[b]) for b in range(2)]
     ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "free_in", "done", "free_out")}
     h2d = dL.numel() * dL.element_size() + cam_bytes
     d2h = rast.image.numel() * rast.image.element_size()
@@ -441,12 +461,9 @@ def run_e2e(args, rast, g, dL, grads, step, pixels, dev):
     def compute_and_download(k):
         b = k % 2
         main.wait_event(ev["in"][b])
-        dL.copy_(stage_dl[b], non_blocking=True)
-        rast.cams_dev.copy_(stage_cam[b], non_blocking=True)
-        ev["free_in"][b].record(main)
-        step.replay()
         main.wait_event(ev["free_out"][b])
-        stage_img[b].copy_(rast.image, non_blocking=True)
+        steps[b].replay()
+        ev["free_in"][b].record(main)
         ev["done"][b].record(main)
         s_out.wait_event(ev["done"][b])
         with torch.cuda.stream(s_out):
@@ -473,6 +490,7 @@ def run_e2e(args, rast, g, dL, grads, step, pixels, dev):
     if rast.read_status():
         raise RuntimeError("device status during the end-to-end run")
     ms = e0.elapsed_time(e1) / k
+    del steps
     return {"value": pixels / (ms * 1e3), "unit": "Mpixel/s", "ms_per_step": ms,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "note": "per step: camera + dL/dimage host->device, image device->host (pinned, overlapped "
