@@ -9,6 +9,10 @@ paper's training.
 
 Parameters are held raw (log-scales, opacity logits) and activated with PyTorch
 elementwise ops; the rasterizer takes activated values (hgs_gaussians).
+
+With mip=True the model is Mip-Splatting-HGS: the 3D smoothing filter (mip.py) joins
+the activation, with sigma_f from the training cameras, and the rasterizer runs its
+2D filter (hgs_config.mip, low-pass 0.1 as in Mip-Splatting).
 """
 from __future__ import annotations
 
@@ -17,6 +21,7 @@ import math
 import torch
 
 from . import hgs as H
+from . import mip as M
 from .rasterizer import Gaussians, HGSRasterize, Rasterizer
 
 # base learning rates (3D-GS defaults; normals per the paper)
@@ -46,14 +51,23 @@ class HalfGaussianModel(torch.nn.Module):
         sh = torch.as_tensor(sc.sh, dtype=torch.float32).reshape(sc.means.shape[0], -1, 3)
         self.sh_dc = p(sh[:, :1])
         self.sh_rest = p(sh[:, 1:])
+        self.register_buffer("filter_sigma", None)      # Mip-Splatting's 3D filter, if set
+
+    def set_3d_filter(self, cams, k=0.2):
+        """sigma_f of each kernel from the training cameras (Mip-Splatting recomputes it
+        from time to time; it is not differentiated)."""
+        self.filter_sigma = M.filter_sigma(self.means, cams, k)
 
     @property
     def n(self):
         return int(self.means.shape[0])
 
     def activated(self):
-        return (self.means, torch.exp(self.log_scales), self.quats, self.normals, torch.sigmoid(self.logit_o1),
-                torch.sigmoid(self.logit_o2), torch.cat([self.sh_dc, self.sh_rest], 1).reshape(self.n, -1))
+        scales, o1, o2 = torch.exp(self.log_scales), torch.sigmoid(self.logit_o1), torch.sigmoid(self.logit_o2)
+        if self.filter_sigma is not None:
+            scales, o1, o2 = M.apply_3d_filter(scales, o1, o2, self.filter_sigma)
+        return (self.means, scales, self.quats, self.normals, o1, o2,
+                torch.cat([self.sh_dc, self.sh_rest], 1).reshape(self.n, -1))
 
     def render(self, rast: Rasterizer):
         return HGSRasterize.apply(rast, self.sh_degree, *self.activated())
@@ -78,14 +92,21 @@ def render_targets(sc, cams, config=None, device="cuda"):
     return r.forward(Gaussians.from_scene(sc, device)).clone()
 
 
-def fit(init_scene, cams, target, iters=100, config=None, scene_extent=1.0, device="cuda", log_every=0):
+def fit(init_scene, cams, target, iters=100, config=None, scene_extent=1.0, device="cuda", log_every=0,
+        mip=False, filter_every=100):
     """Adam on an L1 loss between the render of `init_scene`'s parameters and `target`
-    (packed images of all views).  Returns (model, list of per-iteration losses)."""
+    (packed images of all views).  mip: Mip-Splatting-HGS (3D filter refreshed every
+    `filter_every` iterations, 2D filter in the rasterizer).  Returns (model, list of
+    per-iteration losses)."""
     model = HalfGaussianModel(init_scene, device)
-    rast = Rasterizer(cams, model.n, config or H.make_config(), device=device)
+    if config is None:
+        config = H.make_config(mip=True, lowpass=0.1) if mip else H.make_config()
+    rast = Rasterizer(cams, model.n, config, device=device)
     opt = torch.optim.Adam(model.param_groups(scene_extent), eps=1e-15)
     losses = []
     for it in range(iters):
+        if mip and it % filter_every == 0:
+            model.set_3d_filter(cams)
         decay_lrs(opt, it)
         opt.zero_grad(set_to_none=True)
         img = model.render(rast)

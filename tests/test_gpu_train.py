@@ -33,6 +33,19 @@ def test_fit_lowers_the_loss(cuda_ok):
         assert p.grad is None or bool(p.grad.isfinite().all())
 
 
+def test_fit_mip_splatting_hgs_lowers_the_loss(cuda_ok):
+    """Mip-Splatting-HGS (3D filter in the activation, 2D filter in the rasterizer)
+    fitted to targets rendered the same way."""
+    from paper_2406_02720_b300 import hgs as H, train
+    hidden, init, cams = _setup(53)
+    cfg = H.make_config(mip=True, lowpass=0.1)
+    target = train.render_targets(hidden, cams, cfg)
+    model, losses = train.fit(init, cams, target, iters=150, mip=True)
+    assert model.filter_sigma is not None and bool((model.filter_sigma > 0).all())
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])
+
+
 def test_autograd_matches_the_adjoint_call(cuda_ok):
     import torch
     from paper_2406_02720_b300 import hgs as H
