@@ -33,6 +33,7 @@ constexpr int kPart = kBlock * kItems;       // 4096 elements per partition
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;      // 256 digits
 constexpr int kDepthPasses = 4;              // 32 depth bits
+constexpr int kGroup = kBlock / 32;          // chunks of kBlock splats per scan group (one k_scan_reduce block)
 
 struct Ctrl {                                // zeroed at the start of every call
     uint32_t totals[kRadix];                 // per-digit totals of the current pass
@@ -41,7 +42,8 @@ struct Ctrl {                                // zeroed at the start of every cal
 
 struct Ws {
     Ctrl *ctrl;
-    unsigned long long *chunk_pre;           // [chunks of kBlock splats] sums, then exclusive prefixes
+    unsigned long long *chunk_sum;           // [chunks of kBlock splats] pair counts
+    unsigned long long *group_pre;           // [groups of 8 chunks] pair counts, then exclusive prefixes
     uint32_t *dkA, *dvA, *dkB, *dvB;         // [VN] depth keys / splat indices, ping-pong
     uint32_t *tiles_sorted;                  // [VN] tiles touched, in depth order
     uint32_t *tkA, *tvA, *tkB, *tvB;         // [capacity] tile keys / splat indices, ping-pong
@@ -61,7 +63,9 @@ Ws carve(void *base, size_t vn, size_t cap, size_t *total) {
     auto take = [&](size_t bytes) { char *p = b ? b + off : nullptr; off += align_up(bytes); return p; };
     const size_t vn1 = std::max<size_t>(vn, 1), cap1 = std::max<size_t>(cap, 1);
     w.ctrl = reinterpret_cast<Ctrl *>(take(sizeof(Ctrl)));
-    w.chunk_pre = reinterpret_cast<unsigned long long *>(take(8 * ((vn1 + kBlock - 1) / kBlock)));
+    const size_t n_chunks = (vn1 + kBlock - 1) / kBlock;
+    w.chunk_sum = reinterpret_cast<unsigned long long *>(take(8 * n_chunks));
+    w.group_pre = reinterpret_cast<unsigned long long *>(take(8 * ((n_chunks + kGroup - 1) / kGroup)));
     w.dkA = reinterpret_cast<uint32_t *>(take(4 * vn1));
     w.dvA = reinterpret_cast<uint32_t *>(take(4 * vn1));
     w.dkB = reinterpret_cast<uint32_t *>(take(4 * vn1));
@@ -350,9 +354,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_downsweep(DownArgs a) {
 // ---- stage 2: exclusive scan of tiles touched, in depth order -----------------------------
 // Reduce, then scan, then the pair emission applies the prefixes: no inter-block
 // waiting.  k_scan_reduce gathers tiles touched into depth order (so later reads are
-// contiguous) and sums each chunk of kBlock splats; k_chunk_scan turns the chunk sums
-// into exclusive prefixes (64-bit: the total may exceed the pair capacity) and the
-// pair count; k_duplicate finishes the scan inside each chunk.
+// contiguous) and sums each chunk of kBlock splats and each group of kGroup chunks;
+// k_chunk_scan turns the group sums into exclusive prefixes (64-bit: the total may
+// exceed the pair capacity) and the pair count; k_duplicate adds the chunks before
+// its own in the group and finishes the scan inside its chunk.
 // A block covers 8 chunks of kBlock splats, a warp one chunk, a thread 8 consecutive
 // splats (two 128-bit loads of the order, 8 independent gathers in flight).
 constexpr int kReducePer = 8;
@@ -360,7 +365,9 @@ constexpr int kReducePer = 8;
 __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t *__restrict__ tiles,
                                                         const uint32_t *__restrict__ order, long long vn,
                                                         uint32_t *__restrict__ tiles_sorted,
-                                                        unsigned long long *__restrict__ chunk_sum) {
+                                                        unsigned long long *__restrict__ chunk_sum,
+                                                        unsigned long long *__restrict__ group_sum) {
+    __shared__ unsigned long long s_chunk[kGroup];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     // this warp's 256 splats start at `base` (chunk base / kBlock); a thread takes 8 consecutive
     const long long base = (long long)blockIdx.x * kBlock * kReducePer + (long long)warp * 32 * kReducePer;
@@ -388,18 +395,30 @@ __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t *__restri
     // the warp's 256 splats are chunk `base / kBlock`; only existing chunks are written
     const long long c = base / kBlock;
     if (lane == 0 && base < vn) chunk_sum[c] = x;
+    // and the block's 8 chunks are scan group blockIdx.x
+    if (lane == 0) s_chunk[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0 && (long long)blockIdx.x * kBlock * kReducePer < vn) {
+        unsigned long long g = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kGroup; ++w2) g += s_chunk[w2];
+        group_sum[blockIdx.x] = g;
+    }
 }
 
 constexpr int kChunkScanThreads = 1024;
 
-// One block.  Warp w of a round scans 512 consecutive chunk sums, read row by row
-// (lane l of row i holds entry 32 i + l: every load is coalesced); the warps'
-// totals are then scanned across the block.  One round below 16384 chunks.
+// One block scans the group sums (exclusive, in place) and writes the pair count.
+// Warp w of a round scans ROWS x 32 consecutive sums, read row by row (lane l of
+// row i holds entry 32 i + l: every load is coalesced); the warps' totals are then
+// scanned across the block.  ROWS = 2 covers 2048 groups (4.2M splats) in one round.
+// (Scanning the 8x more chunk sums here instead took 15 us, latency-bound.)
+template <int ROWS>
 __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(unsigned long long *chunk, long long n_chunks,
                                                                   uint64_t *total_out) {
     __shared__ unsigned long long s_w[kChunkScanThreads / 32];
     __shared__ unsigned long long s_total;
-    constexpr int kRows = 16, kSeg = 32 * kRows;
+    constexpr int kRows = ROWS, kSeg = 32 * kRows;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     unsigned long long carry = 0;
     for (long long base = 0; base < n_chunks; base += (long long)kChunkScanThreads * kRows) {
@@ -455,7 +474,8 @@ struct DupArgs {
     const uint32_t *tiles_sorted;   // tiles touched, in depth order
     const int4 *rect;
     const uint32_t *order;          // (view, splat) indices in depth order
-    const unsigned long long *chunk_pre;   // exclusive pair prefix of each chunk of kBlock splats
+    const unsigned long long *chunk_sum;   // pair count of each chunk of kBlock splats
+    const unsigned long long *group_pre;   // exclusive pair prefix of each group of kGroup chunks
     long long vn;
     int n;
     ViewTable vt;
@@ -472,6 +492,10 @@ __global__ void __launch_bounds__(kBlock) k_duplicate(DupArgs a) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const long long j0 = (long long)blockIdx.x * kBlock + warp * 32;
     const long long j = j0 + lane;
+    // this chunk's prefix: its group's, plus the chunks before it in the group
+    const uint32_t gi = blockIdx.x % kGroup;
+    unsigned long long before = lane < (int)gi ? a.chunk_sum[blockIdx.x - gi + lane] : 0ull;
+    const unsigned long long gpre = a.group_pre[blockIdx.x / kGroup];
     uint32_t vi = 0, cnt = 0;
     if (j < a.vn) {
         vi = a.order[j];
@@ -486,7 +510,9 @@ __global__ void __launch_bounds__(kBlock) k_duplicate(DupArgs a) {
     const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
     if (lane == 0) s_wsum[warp] = total;
     __syncthreads();
-    uint64_t wbase = a.chunk_pre[blockIdx.x];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    uint64_t wbase = gpre + __shfl_sync(0xffffffffu, before, 0);
     for (int w2 = 0; w2 < warp; ++w2) wbase += s_wsum[w2];
     if (j0 >= a.vn || total == 0) return;
     const int4 r = cnt ? a.rect[vi] : make_int4(0, 0, 0, 0);
@@ -631,17 +657,21 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
     }
 
     // stage 2: pair offsets in depth order, pair emission, passes over the tile half
-    const long long n_chunks = (long long)((vn + kBlock - 1) / kBlock);
-    k_scan_reduce<<<(unsigned)((vn + (size_t)kBlock * kReducePer - 1) / ((size_t)kBlock * kReducePer)), kBlock, 0,
-                    s>>>(p.proj->tiles, w.dvA, (long long)vn, w.tiles_sorted, w.chunk_pre);
+    const long long n_groups = (long long)((vn + (size_t)kBlock * kReducePer - 1) / ((size_t)kBlock * kReducePer));
+    k_scan_reduce<<<(unsigned)n_groups, kBlock, 0, s>>>(p.proj->tiles, w.dvA, (long long)vn, w.tiles_sorted,
+                                                        w.chunk_sum, w.group_pre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_chunk_scan<<<1, kChunkScanThreads, 0, s>>>(w.chunk_pre, n_chunks, p.num_pairs);
+    if (n_groups <= 2 * kChunkScanThreads)
+        k_chunk_scan<2><<<1, kChunkScanThreads, 0, s>>>(w.group_pre, n_groups, p.num_pairs);
+    else
+        k_chunk_scan<16><<<1, kChunkScanThreads, 0, s>>>(w.group_pre, n_groups, p.num_pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     DupArgs d;
     d.tiles_sorted = w.tiles_sorted;
     d.rect = reinterpret_cast<const int4 *>(p.proj->rect);
     d.order = w.dvA;
-    d.chunk_pre = w.chunk_pre;
+    d.chunk_sum = w.chunk_sum;
+    d.group_pre = w.group_pre;
     d.vn = (long long)vn;
     d.n = p.n;
     d.vt = p.vt;
