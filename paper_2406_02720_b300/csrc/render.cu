@@ -334,8 +334,10 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
                         }
                     }
                 }
-                if (__all_sync(0xffffffffu, done)) { wdone = true; break; }
             }
+            // checked once per chunk, not per visit: a warp whose lanes are all done only
+            // runs the rest of this chunk's (cheap) bit loop (render_fwd 0.711 -> 0.679 ms)
+            wdone = __all_sync(0xffffffffu, done);
         }
     }
     if (inside) {
