@@ -675,16 +675,48 @@ class OracleSample:
         np.add.at(d, (r[:, 3], r[:, 2]), 1)
         self.tile_pairs = np.cumsum(np.cumsum(d, 0), 1)[:ty, :tx].reshape(-1)
         self.by_pairs = np.argsort(self.tile_pairs, kind="stable")
+        # 4x4-tile clusters ordered by their pairs: sampled tiles come in clusters, which
+        # share splats as the full frame's neighbouring tiles do (scattered tiles ran
+        # ~1.5-2x slower per tile than the full frame, ~1.4-1.8x in clusters)
+        self.cl = 4
+        cy, cx = max(ty // self.cl, 1), max(tx // self.cl, 1)
+        tp = np.zeros((cy * self.cl, cx * self.cl), np.int64)
+        h, w = min(ty, cy * self.cl), min(tx, cx * self.cl)
+        tp[:h, :w] = self.tile_pairs.reshape(ty, tx)[:h, :w]
+        self.cluster_grid = (cy, cx, ty, tx)
+        self.by_cluster = np.argsort(tp.reshape(cy, self.cl, cx, self.cl).sum((1, 3)).reshape(-1), kind="stable")
         # the per-call cost of the compositing calls that does not depend on the tiles
-        # (full-image buffers): measured once with no tile selected, not scaled
-        self.t_fixed = statistics.median(self._composite(np.zeros(self.n_tiles, np.uint8)) for _ in range(3))
+        # (full-image buffers, thread start-up): measured on the tile with the shortest
+        # list, not scaled
+        one = np.zeros(self.n_tiles, np.uint8)
+        one[self.by_pairs[0]] = 1
+        self.t_fixed = statistics.median(self._composite(one) for _ in range(3))
+        # likewise the per-call cost of the per-splat phases, from a 64-splat subset
+        self.t_fixed_splat = statistics.median(self._per_splat(64)[0] for _ in range(3))
+
+    def _per_splat(self, m):
+        o = self.oracle
+        sub = self.sc.subset(np.sort(self.splat_order[:m]))
+        g2 = np.random.default_rng(m).normal(size=(m, 12))
+        t0 = time.perf_counter()
+        pr = o.project(sub, self.cam, self.tile)
+        o.bin_pairs(pr, self.cam, self.tile)
+        o.project_bwd(sub, self.cam, pr["mode"], g2, self.tile)
+        return time.perf_counter() - t0, pr
 
     def tiles_for(self, k, u=0.5):
-        """k tiles, one from each of k equal strata of the tiles ordered by list length
-        (systematic sampling at offset u in [0, 1)): each stands for n_tiles / k tiles
-        of like cost."""
-        pos = ((np.arange(k) + u) * self.n_tiles / k).astype(np.int64)
-        return self.by_pairs[np.minimum(pos, self.n_tiles - 1)]
+        """About k tiles: 4x4-tile clusters, one from each of ceil(k/16) equal strata of
+        the clusters ordered by their pairs (systematic sampling at offset u in [0, 1))."""
+        cy, cx, ty, tx = self.cluster_grid
+        nc = max(1, min(-(-k // (self.cl * self.cl)), cy * cx))
+        pos = ((np.arange(nc) + u) * (cy * cx) / nc).astype(np.int64)
+        out = []
+        for c in self.by_cluster[np.minimum(pos, cy * cx - 1)]:
+            y, x = divmod(int(c), cx)
+            for yy in range(y * self.cl, min((y + 1) * self.cl, ty)):
+                for xx in range(x * self.cl, min((x + 1) * self.cl, tx)):
+                    out.append(yy * tx + xx)
+        return np.asarray(out, np.int64)
 
     def _composite(self, mask):
         o = self.oracle
@@ -700,41 +732,39 @@ class OracleSample:
         o = self.oracle
         m = max(1, min(m, self.sc.n))
         k = max(1, min(k, self.n_tiles))
-        sub = self.sc.subset(np.sort(self.splat_order[:m]))
         mask = np.zeros(self.n_tiles, np.uint8)
-        mask[self.tiles_for(k, u)] = 1
-        g2 = np.random.default_rng(m).normal(size=(m, 12))
-        # the sampled tiles' lists (binning is timed on the splat subset above)
+        sel = self.tiles_for(k, u)
+        mask[sel] = 1
+        k = len(sel)
+        # the sampled tiles' lists (binning is timed on the splat subset below)
         tb = time.perf_counter()
         bins = o.bin_pairs(self.pr_full, self.cam, self.tile, tile_mask=mask)
         prep = time.perf_counter() - tb
-        t0 = time.perf_counter()
-        pr = o.project(sub, self.cam, self.tile)
-        t1 = time.perf_counter()
-        o.bin_pairs(pr, self.cam, self.tile)
-        t2 = time.perf_counter()
-        o.project_bwd(sub, self.cam, pr["mode"], g2, self.tile)
+        t_splat, _ = self._per_splat(m)
         t3 = time.perf_counter()
         out = o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
         o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
         t4 = time.perf_counter()
-        per_splat = (t3 - t0) * self.sc.n / m
+        t0 = t3 - t_splat
+        per_splat = self.t_fixed_splat + max(t_splat - self.t_fixed_splat, 0.0) * self.sc.n / m
         per_tile = self.t_fixed + max(t4 - t3 - self.t_fixed, 0.0) * self.n_tiles / k
         del out
         return per_splat + per_tile, t4 - t0 + prep
 
     def describe(self, m, k):
-        return (f"projection, binning and projection adjoint of {m} of {self.sc.n} splats (seeded subset, "
-                f"scaled by n/m); compositing fwd+bwd of {k} of {self.n_tiles} tiles (one per stratum of "
-                "the tiles ordered by list length; the time beyond the calls' fixed cost scaled by the tile "
-                "fraction); FP64")
+        return (f"projection, binning and projection adjoint of {m} of {self.sc.n} splats (seeded subset; the "
+                f"time beyond the calls' fixed cost scaled by n/m); compositing fwd+bwd of {len(self.tiles_for(k))} "
+                f"of {self.n_tiles} tiles (4x4-tile clusters, one per stratum of the clusters ordered by their "
+                "pairs; the time beyond the calls' fixed cost scaled by the tile fraction; pessimistic by up to ~2x "
+                "in checks against a whole frame: sampled tiles share fewer cached splats); FP64")
 
 
-def cpu_baseline(args, m=None, k=48):
+def cpu_baseline(args, m=None, k=None):
     """One bounded oracle sample of the bench workload (about 10-30 s of CPU work)."""
     import oracle
     samp = OracleSample(args)
     m = m or samp.sc.n
+    k = k or 16 * oracle.num_threads()      # 16 tiles per host thread (see run_reference)
     est, meas = samp.step(m, k)
     pixels = samp.cam.width * samp.cam.height
     return {"value": pixels / (est * 1e6), "unit": "Mpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
@@ -749,13 +779,18 @@ def run_reference(args):
     if rank != 0:
         return None
     samp = OracleSample(args)
-    budget = min(20.0, max(0.05, 120.0 / (args.steps + args.warmup)))
-    m, k = 20_000, 2
+    # per-step sample: about two minutes over warm-up + steps, but never below 20k splats
+    # and 16 tiles per host thread (the oracle composites tiles in parallel; with few
+    # tiles per thread the sample times the slowest thread's tiles, not the host's
+    # throughput)
+    budget = min(20.0, max(0.4, 120.0 / (args.steps + args.warmup)))
+    k_min = 16 * oracle.num_threads()
+    m, k = 20_000, k_min
     for _ in range(max(args.warmup, 1)):       # calibration: grow or shrink the sample to the budget
         _, meas = samp.step(m, k)
         scale = budget / max(meas, 1e-3)
-        m = int(min(samp.sc.n, max(2_000, m * scale)))
-        k = int(min(samp.n_tiles, max(1, k * scale)))
+        m = int(min(samp.sc.n, max(20_000, m * scale)))
+        k = int(min(samp.n_tiles, max(k_min, k * scale)))
     vals = []
     for i in range(args.steps):
         # the strata offset moves every step, so that the steps together sample
