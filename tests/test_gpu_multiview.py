@@ -54,3 +54,38 @@ def test_batched_equals_per_view(cuda_ok, tile, batch):
         np.testing.assert_allclose(gb, gp, rtol=1e-3, atol=1e-5 * np.abs(gp).max())
         bad, _ = grad_close(gb, tot[k])
         assert bad.mean() < 2e-3, k
+
+
+def test_many_views_pairs_equal_per_view_launches(cuda_ok):
+    """4.5M (view, splat) entries in one launch sequence (the pair-offset scan then runs
+    over more than 2048 groups of 8 chunks: the 16-row scan) give exactly the
+    sorted pairs of five single-view launches (each pinned against the oracle's sort
+    elsewhere), with tile ids offset by view and splat ids by n * view."""
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
+    rng = np.random.default_rng(61)
+    n = 900_000
+    sc = scenes.scene_uniform(rng, n, [-2, -2, -2], [2, 2, 2], -4.6, 0.5, 1.5, 0)
+    cams = scenes.fibonacci_cameras(5, radius=6.0, resolutions=[(320, 240), (256, 192), (320, 180), (200, 200),
+                                                               (288, 216)])
+    g = Gaussians.from_scene(sc)
+    cfg = H.make_config()
+    batched = Rasterizer(cams, n, cfg, keep_keys=True)
+    batched.forward(g)
+    bk, bi = (x.cpu().numpy() for x in batched.sorted_pairs())
+    bk, bi = bk.view(np.uint64), bi.view(np.uint32)
+    assert batched.read_status() == 0
+    assert -(-len(cams) * n // 2048) > 2048             # more scan groups than the 2-row scan holds
+    off = 0
+    parts_k, parts_i = [], []
+    for v, cam in enumerate(cams):
+        r = Rasterizer([cam], n, cfg, keep_keys=True)
+        r.forward(g)
+        k, i = (x.cpu().numpy() for x in r.sorted_pairs())
+        k, i = k.view(np.uint64), i.view(np.uint32)
+        parts_k.append(k + (np.uint64(off) << np.uint64(32)))
+        parts_i.append(i + np.uint32(v * n))
+        tx, ty = oracle.grid(cam, (16, 16))
+        off += tx * ty
+    assert np.array_equal(bk, np.concatenate(parts_k))
+    assert np.array_equal(bi, np.concatenate(parts_i))
