@@ -578,26 +578,31 @@ __global__ void __launch_bounds__(kBlock) k_ranges(const uint32_t *__restrict__ 
     }
 }
 
-int g_sweep_blocks = 0, g_aux_blocks = 0;
+// Resident blocks per SM of the downsweep and of the upsweep/ranges kernels (the same
+// on every device of this architecture); grids are these times the current device's
+// SM count.
+int g_occ_sweep = 0, g_occ_aux = 0;
 
 void init_launch_shapes() {
-    if (g_sweep_blocks) return;
-    const int sms = num_sms();
+    if (g_occ_sweep) return;
     int occ = 0, occ2 = 0;
     cudaFuncSetAttribute(k_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
     cudaFuncSetAttribute(k_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_downsweep<false>, kBlock, sizeof(DownSmem));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_upsweep, kBlock, 0);
-    g_sweep_blocks = sms * std::max(occ, 1);
-    g_aux_blocks = sms * std::max(occ2, 1);
+    g_occ_aux = std::max(occ2, 1);
+    g_occ_sweep = std::max(occ, 1);
 }
+
+int sweep_blocks() { return num_sms() * g_occ_sweep; }
+int aux_blocks() { return num_sms() * g_occ_aux; }
 
 // One radix pass over cnt elements: upsweep, digit scan, downsweep.
 cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout, uint64_t *kout64,
                        const float *depth, Count cnt, size_t max_elems, int shift, const Ws &w, int *status,
                        cudaStream_t s) {
     const int parts = (int)std::max<size_t>((max_elems + kPart - 1) / kPart, 1);
-    k_upsweep<<<std::min(parts, g_aux_blocks), kBlock, 0, s>>>(kin, cnt, shift, w.counts, w.parts_stride);
+    k_upsweep<<<std::min(parts, aux_blocks()), kBlock, 0, s>>>(kin, cnt, shift, w.counts, w.parts_stride);
     k_digit_scan<<<kRadix, kBlock, 0, s>>>(w.counts, cnt, w.parts_stride, w.ctrl);
     DownArgs a{};
     a.kin = kin;
@@ -612,7 +617,7 @@ cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
     a.stride = w.parts_stride;
     a.ctrl = w.ctrl;
     a.status = status;
-    const int grid = std::min(parts, g_sweep_blocks);
+    const int grid = std::min(parts, sweep_blocks());
     if (kout64)
         k_downsweep<true><<<grid, kBlock, sizeof(DownSmem), s>>>(a);
     else
@@ -692,7 +697,7 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     const uint32_t *tiles_sorted = (tile_passes % 2) ? w.tkB : w.tkA;
-    k_ranges<<<g_aux_blocks, kBlock, 0, s>>>(tiles_sorted, cnt_k, total_tiles, p.ranges, p.status);
+    k_ranges<<<aux_blocks(), kBlock, 0, s>>>(tiles_sorted, cnt_k, total_tiles, p.ranges, p.status);
     return cudaGetLastError();
 }
 

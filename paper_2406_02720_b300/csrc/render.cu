@@ -267,8 +267,9 @@ __device__ __forceinline__ void warp_block(const TileInfo &ti, int TH_, int row0
 
 // Blocks per tile: each stages the tile's whole list for its own rows.  Fewer warps
 // per block wait for one another at the batch barriers, at the price of staging each
-// list once per block.  Measured at 3M splats, 1080p, 16x16 tiles: forward 0.726 ms
-// with 2 blocks per tile vs 0.731 with 1; backward 1.411 ms with 1 vs 1.447 with 2.
+// list once per block.  Measured at 3M splats, 1080p, 16x16 tiles: forward 0.675 ms
+// with 2 blocks per tile vs 0.683 with 1; backward 1.411 ms with 1 vs 1.447 with 2 (an
+// earlier version of the kernel).
 template <bool FWD, int TW, int TH>
 constexpr int kSplit = (FWD && TW * TH >= 256) ? 2 : 1;
 
@@ -620,13 +621,15 @@ cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
         kern<<<items, NT, 0, s>>>(p);
         return cudaGetLastError();
     }
-    static int blocks = 0;
-    if (!blocks) {
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
-        blocks = num_sms() * std::max(occ, 1);
+    // resident blocks per SM (the same on every device of this architecture), times the
+    // current device's SM count
+    static int occ = 0;
+    if (!occ) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, 0);
+        occ = std::max(o, 1);
     }
-    kern<<<std::min(blocks, items), NT, 0, s>>>(p);
+    kern<<<std::min(num_sms() * occ, items), NT, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -656,7 +659,8 @@ template <bool FWD, int TW, int TH>
 cudaError_t dispatch_batch(const RenderLaunch &p, cudaStream_t s) {
     // default: the tile's pixel count forward, twice that backward (capped at 512), where
     // longer batches average out the uneven per-warp work between block barriers
-    // (16x16 tiles at 3M splats: forward 0.78 vs 0.79 ms at 256 / 512, backward 1.50 vs 1.48)
+    // (16x16 tiles at 3M splats: forward 0.677 / 0.697 / 0.886 ms at 256 / 128 / 512;
+    // backward 1.48 at 512 vs 1.50 at 256 in an earlier version of the kernel)
     const int batch = p.cfg.batch ? p.cfg.batch : (FWD ? TW * TH : std::min(2 * TW * TH, 512));
     switch (batch) {
         case 32: return launch_c<TW, TH, 32, FWD>(p, s);
