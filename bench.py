@@ -322,7 +322,7 @@ def alg_bytes(n, n_pairs, total_tiles):
 #   contrib: backward adjoint of one composited pair (T rebuilt by division,
 #            colour-behind recurrence as one dot product, 12 gradients)     39 FP32 + 1 MUFU
 #   red    : fold of 12 gradients over lane pairs (one shuffle+add
-#            level, all 32 lanes) when more than 16 lanes contribute    384 FP32
+#            level, all 32 lanes) when more than 12 lanes contribute    384 FP32
 OPS = {"fwd": {"fp32": {"fwd_visit": 8, "fwd_full": 16, "fwd_comp": 7}, "mufu": {"fwd_full": 3}},
        "bwd": {"fp32": {"bwd_visit": 8, "bwd_full": 16, "bwd_contrib": 39, "bwd_warp_red": 384},
                "mufu": {"bwd_full": 3, "bwd_contrib": 1}}}

@@ -300,7 +300,7 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
  *   [0] forward (pixel, splat) iterations  [1] forward full evaluations (past the
  *   3-sigma/opacity cut-off)  [2] splats composited  [3] backward iterations
  *   [4] backward full evaluations  [5] backward contributing pairs
- *   [6] backward (warp, splat) visits with more than 16 contributing lanes (folded
+ *   [6] backward (warp, splat) visits with more than 12 contributing lanes (folded
  *   by one shuffle level before the atomics)  [7] reserved (0). */
 hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                             const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,

@@ -357,11 +357,14 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
 // ---- backward ------------------------------------------------------------------------
 
 // A splat's 12 gradients from the lanes of a warp go to global memory as float4
-// atomic adds (3 per lane).  When more than 16 lanes contribute, one xor-shuffle
-// level first folds lane l + 16 into lane l, so at most 16 lanes issue atomics:
-// 24 instructions instead of a full 5-level reduction (~62), at the price of more
-// atomic traffic, which the L2 absorbs (measured: fastest of full reduction, direct
-// atomics from up to 1..32 lanes, and this split at 16).
+// atomic adds (3 per lane).  When more than kFoldAbove lanes contribute, one
+// xor-shuffle level first folds lane l + 16 into lane l, so at most 16 lanes issue
+// atomics: 24 instructions instead of a full 5-level reduction (~62), at the price of
+// more atomic traffic, which the L2 absorbs (measured: fastest of full reduction,
+// direct atomics from up to 1..32 lanes, and this split; at 3M splats, 1080p the
+// backward takes 1.333 / 1.325 / 1.322 / 1.327 / 1.393 ms folding above 8 / 10 / 12 /
+// 16 / 24 contributing lanes).
+constexpr int kFoldAbove = 12;
 __device__ __forceinline__ void atomic_add12(float *dst, const float g[12]) {
     float4 *d4 = reinterpret_cast<float4 *>(dst);
     atomicAdd(d4, make_float4(g[0], g[1], g[2], g[3]));
@@ -494,7 +497,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 const unsigned any = __ballot_sync(0xffffffffu, contrib);
                 if (!any) continue;
                 float *dst = grad + 12 * (size_t)s.id[k];
-                if (__popc(any) <= 16) {
+                if (__popc(any) <= kFoldAbove) {
                     if (contrib) atomic_add12(dst, gr);
                 } else {
                     if (COUNT && lane == 0) ++c_red;
