@@ -65,3 +65,22 @@ def test_mip_without_lowpass_is_bitwise_the_plain_path(cuda_ok):
     b = gpu_render(sc, cams, lowpass=0.0, mip=False)
     assert np.array_equal(a["rec"], b["rec"])
     assert np.array_equal(a["images"][0], b["images"][0])
+
+
+def test_mip_with_per_half_rectangles(cuda_ok):
+    """mip with rect_mode 1: binning bit-exact against the oracle (its per-half test
+    uses the unscaled opacities on both sides), images and gradients within tolerance."""
+    rng = np.random.default_rng(47)
+    sc = scenes.scene_uniform(rng, 1500, [-1.6, -1.0, 2.0], [1.6, 1.0, 7.0], -3.6, 0.6, 1.2, 1)
+    k = rng.random(sc.n)
+    sc.opac2[k < 0.3] = 0.002                          # one half below 1/255
+    cams = [scenes.identity_camera(160, 96, 110.0, bg=(0.1, 0.1, 0.2))]
+    ref = oracle.render(sc, cams[0], rect_mode=1, mip=True)
+    dL = masked_upstream(scenes.upstream_grad(48, cams), [ref])
+    out = gpu_render(sc, cams, dL=dL, rect_mode=1, mip=True)
+    assert np.array_equal(out["keys"], ref["bins"]["keys"]) and np.array_equal(out["ids"], ref["bins"]["ids"])
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    gref = oracle.render_bwd(sc, cams[0], dL[0], proj=ref["proj"], bins=ref["bins"], mip=True)
+    for f in FIELDS:
+        bad, _ = grad_close(out["grads"][f], gref[f])
+        assert bad.mean() < 2e-3, (f, int(bad.sum()), bad.size)

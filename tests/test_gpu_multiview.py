@@ -89,3 +89,23 @@ def test_many_views_pairs_equal_per_view_launches(cuda_ok):
         off += tx * ty
     assert np.array_equal(bk, np.concatenate(parts_k))
     assert np.array_equal(bi, np.concatenate(parts_i))
+
+
+def test_maximum_view_count(cuda_ok):
+    """HGS_MAX_VIEWS (256) cameras of uneven small sizes in one launch sequence: every
+    view's image matches the oracle's render of that view alone."""
+    from paper_2406_02720_b300 import hgs as H
+    from paper_2406_02720_b300.rasterizer import Gaussians, Rasterizer
+    rng = np.random.default_rng(63)
+    sc = scenes.scene_uniform(rng, 400, [-2, -2, -2], [2, 2, 2], -3.0, 0.5, 1.5, 1)
+    sizes = [(16, 16), (24, 16), (40, 24), (17, 33)]
+    cams = scenes.fibonacci_cameras(H.HGS_MAX_VIEWS, radius=6.0, resolutions=sizes)
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(cams, sc.n, H.make_config())
+    r.forward(g)
+    assert r.read_status() == 0
+    imgs = [x.cpu().numpy() for x in r.images()]
+    for v in list(range(0, H.HGS_MAX_VIEWS, 17)) + [H.HGS_MAX_VIEWS - 1]:
+        ref = oracle.render(sc, cams[v])
+        ok = ~exempt(ref)
+        assert np.abs(imgs[v] - ref["image"])[:, ok].max() <= 1e-4, v
