@@ -649,8 +649,11 @@ def run_mip(args, dev, g, dL, rast0):
 class OracleSample:
     """A bounded sample of the fwd+bwd step for the FP64 oracle.  The per-splat phases
     (projection, binning, projection adjoint) run on a seeded subset of m splats and
-    scale by n/m; compositing and its adjoint run on k seeded tiles of the full scene
-    (its projection is prepared once, untimed) and scale by tiles/k."""
+    scale by n/m; compositing and its adjoint run on about k tiles of the full scene and
+    scale by tiles/k.  The full scene's projection and binning are prepared once,
+    untimed; each compositing sample runs on the sub-problem of its tiles (their lists,
+    with the splats they reference renumbered), which composites those tiles exactly as
+    the full frame does while keeping the oracle's per-call buffers small."""
 
     def __init__(self, args, seed=5):
         import oracle
@@ -664,7 +667,8 @@ class OracleSample:
         self.tile_order = self.rng.permutation(self.n_tiles)
         self.splat_order = self.rng.permutation(self.sc.n)
         self.pr_full = oracle.project(self.sc, self.cam, self.tile)
-        self.g2_sub = None
+        self.bins_full = oracle.bin_pairs(self.pr_full, self.cam, self.tile)
+        self.dL = np.ascontiguousarray(np.asarray(self.dL, np.float64))
         # pairs per tile from the rectangles (a 2-D difference array), to stratify the
         # sampled tiles by list length
         r = self.pr_full["rect"][self.pr_full["tiles"] > 0].astype(np.int64)
@@ -676,8 +680,7 @@ class OracleSample:
         self.tile_pairs = np.cumsum(np.cumsum(d, 0), 1)[:ty, :tx].reshape(-1)
         self.by_pairs = np.argsort(self.tile_pairs, kind="stable")
         # 4x4-tile clusters ordered by their pairs: sampled tiles come in clusters, which
-        # share splats as the full frame's neighbouring tiles do (scattered tiles ran
-        # ~1.5-2x slower per tile than the full frame, ~1.4-1.8x in clusters)
+        # share splats as the full frame's neighbouring tiles do
         self.cl = 4
         cy, cx = max(ty // self.cl, 1), max(tx // self.cl, 1)
         tp = np.zeros((cy * self.cl, cx * self.cl), np.int64)
@@ -718,12 +721,30 @@ class OracleSample:
                     out.append(yy * tx + xx)
         return np.asarray(out, np.int64)
 
+    def _sub_problem(self, mask):
+        """The lists of the masked tiles, their splats renumbered 0..m'-1."""
+        tiles = np.flatnonzero(mask)
+        r = self.bins_full["ranges"][tiles].astype(np.int64)
+        lens = r[:, 1] - r[:, 0]
+        idx = np.concatenate([np.arange(a, b) for a, b in r]) if len(r) else np.zeros(0, np.int64)
+        uniq, inv = np.unique(self.bins_full["ids"][idx], return_inverse=True)
+        ranges = np.zeros((self.n_tiles, 2), np.uint32)
+        ends = np.cumsum(lens)
+        ranges[tiles, 0] = ends - lens
+        ranges[tiles, 1] = ends
+        n = len(self.pr_full["mode"])
+        proj = {k: (v[uniq] if isinstance(v, np.ndarray) and v.ndim and v.shape[0] == n else v)
+                for k, v in self.pr_full.items()}
+        bins = dict(keys=self.bins_full["keys"][idx], ids=inv.astype(np.uint32), ranges=ranges,
+                    n_pairs=int(len(idx)), n_emitted=int(len(idx)))
+        return proj, bins
+
     def _composite(self, mask):
         o = self.oracle
-        bins = o.bin_pairs(self.pr_full, self.cam, self.tile, tile_mask=mask)
+        proj, bins = self._sub_problem(mask)
         t0 = time.perf_counter()
-        o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
-        o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
+        o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
+        o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
         return time.perf_counter() - t0
 
     def step(self, m, k, u=0.5):
@@ -738,12 +759,12 @@ class OracleSample:
         k = len(sel)
         # the sampled tiles' lists (binning is timed on the splat subset below)
         tb = time.perf_counter()
-        bins = o.bin_pairs(self.pr_full, self.cam, self.tile, tile_mask=mask)
+        proj, bins = self._sub_problem(mask)
         prep = time.perf_counter() - tb
         t_splat, _ = self._per_splat(m)
         t3 = time.perf_counter()
-        out = o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
-        o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=self.pr_full, bins=bins)
+        out = o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
+        o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
         t4 = time.perf_counter()
         t0 = t3 - t_splat
         per_splat = self.t_fixed_splat + max(t_splat - self.t_fixed_splat, 0.0) * self.sc.n / m
@@ -755,8 +776,8 @@ class OracleSample:
         return (f"projection, binning and projection adjoint of {m} of {self.sc.n} splats (seeded subset; the "
                 f"time beyond the calls' fixed cost scaled by n/m); compositing fwd+bwd of {len(self.tiles_for(k))} "
                 f"of {self.n_tiles} tiles (4x4-tile clusters, one per stratum of the clusters ordered by their "
-                "pairs; the time beyond the calls' fixed cost scaled by the tile fraction; pessimistic by up to ~2x "
-                "in checks against a whole frame: sampled tiles share fewer cached splats); FP64")
+                "pairs, composited as the sub-problem of their lists; the time beyond the calls' fixed cost "
+                "scaled by the tile fraction); FP64")
 
 
 def cpu_baseline(args, m=None, k=None):
