@@ -418,20 +418,22 @@ def run_e2e(args, rast, g, dL, grads, pixels, dev):
     camera and the upstream image gradient dL/dimage, copied from pinned host memory,
     and its result is the rendered image, copied back to pinned host memory.  PCIe
     copies run on two side streams, double-buffered, so step k+1's upload and step k's
-    download overlap step k's kernels; the on-device copies between the staging
-    buffers and the step's own buffers are captured into the step's graph (one graph
-    per staging buffer), so each step is one graph launch.  (Capturing them as graph
-    branches parallel to the kernels measured no faster.)"""
+    download overlap step k's kernels.  Each staging buffer has its own graph of the
+    step, which reads dL/dimage from it directly and copies the camera in and the image
+    out on the device, so each step is one graph launch.  (Capturing the copies as
+    graph branches parallel to the kernels measured no faster.)"""
     import torch
     from paper_2406_02720_b300.rasterizer import GraphStep
 
     class StagedStep(GraphStep):
+        """The step reading dL/dimage straight from its staging buffer (one graph per
+        buffer), with the camera copied in and the image copied out inside the graph."""
+
         def __init__(self, src_dl, src_cam, dst_img):
-            self.src_dl, self.src_cam, self.dst_img = src_dl, src_cam, dst_img
-            super().__init__(rast, g, dL, grads)
+            self.src_cam, self.dst_img = src_cam, dst_img
+            super().__init__(rast, g, src_dl, grads)
 
         def _body(self, backward):
-            self.dL.copy_(self.src_dl, non_blocking=True)
             self.rast.cams_dev.copy_(self.src_cam, non_blocking=True)
             super()._body(backward)
             self.dst_img.copy_(self.rast.image, non_blocking=True)
