@@ -55,3 +55,20 @@ def test_equal_opacity_copy_is_plain_3dgs(cuda_ok):
     assert np.array_equal(a["images"][0], b["images"][0])
     assert np.array_equal(a["T"][0], b["T"][0])
     assert np.array_equal(a["n_contrib"][0], b["n_contrib"][0])
+
+
+def test_grazing_disks_with_mip(cuda_ok):
+    """The same near-degenerate scene as Mip-Splatting-HGS: the opacity factor's
+    adjoint also runs in the FP64 geometry adjoint of the gathered disks."""
+    sc, cams = scenes.config5(n=60_000)
+    cam = cams[0]
+    ref = oracle.render(sc, cam, mip=True)
+    pr = ref["proj"]
+    dL = masked_upstream(scenes.upstream_grad(106, cams), [ref])
+    out = gpu_render(sc, cams, dL=dL, mip=True)
+    assert len(out["fp64_fwd"]) >= 10                   # the FP64 path is exercised
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    gref = oracle.render_bwd(sc, cam, dL[0], proj=pr, bins=ref["bins"], mip=True)
+    for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
+        bad, _ = grad_close(out["grads"][k], gref[k])
+        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
