@@ -29,7 +29,11 @@
 namespace hgs {
 namespace {
 
+// Splats per block: 128 in the projection, 64 in its adjoint (at 3M splats, degree 3:
+// projection 0.220 / 0.222 / 0.229 ms and adjoint 0.378 / 0.368 / 0.400 ms at
+// 128 / 64 / 256, resident threads per SM held equal).
 constexpr int kProjBlock = 128;
+constexpr int kProjBwdBlock = 64;
 enum { MODE_CULLED = 0, MODE_NORMAL = 1, MODE_STEP = 2, MODE_HALF = 3 };
 
 // Degeneracy test that sends a splat's half-plane terms to the FP64 path: the
@@ -495,15 +499,18 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int ro
     }
 }
 
-struct StageSmem {
-    float mean[3 * kProjBlock];
-    float scale[3 * kProjBlock];
-    float nrm[3 * kProjBlock];
-    float quat[4 * kProjBlock];
-    float o1[kProjBlock];
-    float o2[kProjBlock];
-    float sh[kShStride3 * kProjBlock];
+template <int NB>
+struct StageSmemN {
+    float mean[3 * NB];
+    float scale[3 * NB];
+    float nrm[3 * NB];
+    float quat[4 * NB];
+    float o1[NB];
+    float o2[NB];
+    float sh[kShStride3 * NB];
 };
+using StageSmem = StageSmemN<kProjBlock>;
+using BwdStageSmem = StageSmemN<kProjBwdBlock>;
 
 // Copies the block's parameter rows into shared memory, plus optionally `extra_floats`
 // floats per row from `extra` into `extra_dst` in the same batch of asynchronous copies.
@@ -513,7 +520,8 @@ struct StageSmem {
 // projection 0.219 vs 0.232 ms.  (Copying each thread's own row instead, so that no
 // barrier is needed, was slower: 0.246 ms; so was the adjoint restructured around the
 // barrier, hence it stages everything first.)
-__device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, int rows, StageSmem &sm,
+template <class SM>
+__device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, int rows, SM &sm,
                                              const float *extra = nullptr, int extra_floats = 0,
                                              float *extra_dst = nullptr, bool sh_later = false) {
     const int deg = g.sh_degree, nc3 = 3 * (deg + 1) * (deg + 1);
@@ -545,7 +553,8 @@ struct Params {
     float m[3], s[3], q[4], n[3];
 };
 
-__device__ __forceinline__ Params read_params(const StageSmem &sm, int t) {
+template <class SM>
+__device__ __forceinline__ Params read_params(const SM &sm, int t) {
     Params P;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -562,8 +571,8 @@ __device__ __forceinline__ Params read_params(const StageSmem &sm, int t) {
 // rows (48 floats at stride 52) are read as twelve 128-bit loads, which consecutive
 // threads take from distinct banks; entry j of a row is coefficient j / 3 of
 // channel j % 3.
-template <int DEG>
-__device__ __forceinline__ void sh_colour(const StageSmem &sm, int t, const float Y[16], float out[3]) {
+template <int DEG, class SM>
+__device__ __forceinline__ void sh_colour(const SM &sm, int t, const float Y[16], float out[3]) {
     constexpr int nc = (DEG + 1) * (DEG + 1);
     float acc[3] = {0.0f, 0.0f, 0.0f};
     if (DEG == 3) {
@@ -916,19 +925,19 @@ __device__ __forceinline__ Grads proj_vjp_fp64(const Params &P, const hgs_camera
 // own coefficient row once the coefficients have been read, which halves the
 // shared memory of a block; with several views the rows are separate and summed.
 template <int DEG, bool ONE_VIEW>
-__global__ void __launch_bounds__(kProjBlock, 4) k_project_bwd(ProjBwdLaunch p) {
+__global__ void __launch_bounds__(kProjBwdBlock, 8) k_project_bwd(ProjBwdLaunch p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StageSmem &sm = *reinterpret_cast<StageSmem *>(smem_raw);
+    BwdStageSmem &sm = *reinterpret_cast<BwdStageSmem *>(smem_raw);
     // one view: screen-space gradient rows staged with the parameters; several views:
     // separate SH gradient rows
-    float *extra = reinterpret_cast<float *>(smem_raw + sizeof(StageSmem));
+    float *extra = reinterpret_cast<float *>(smem_raw + sizeof(BwdStageSmem));
     float *gsh_s = ONE_VIEW ? sm.sh : extra;
     const int n = p.g.n;
-    const int base = blockIdx.x * kProjBlock;
-    const int rows = min(kProjBlock, n - base);
+    const int base = blockIdx.x * kProjBwdBlock;
+    const int rows = min(kProjBwdBlock, n - base);
     constexpr int nc = (DEG + 1) * (DEG + 1), nc3 = 3 * nc, shs = DEG == 3 ? kShStride3 : nc3;
     if (!ONE_VIEW)
-        for (int j = threadIdx.x; j < kProjBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
+        for (int j = threadIdx.x; j < kProjBwdBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
     if (ONE_VIEW)
         stage_params(p.g, base, rows, sm, p.grad2d, 12, extra);
     else
@@ -1085,7 +1094,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project_bwd_fp64(ProjBwdLaunch p
 // adjoint either the screen-space gradient rows (one view) or SH gradient rows.
 size_t project_smem_bytes(bool bwd, bool one_view) {
     if (!bwd) return sizeof(StageSmem);
-    return sizeof(StageSmem) + sizeof(float) * (one_view ? 12 : kShStride3) * kProjBlock;
+    return sizeof(BwdStageSmem) + sizeof(float) * (one_view ? 12 : kShStride3) * kProjBwdBlock;
 }
 
 // Grid of the FP64 follow-up kernels: the list length is known only on the device,
@@ -1113,7 +1122,7 @@ cudaError_t launch_project_bwd_deg(const ProjBwdLaunch &p, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_project_bwd<DEG, ONE_VIEW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_project_bwd<DEG, ONE_VIEW><<<div_up(p.g.n, kProjBlock), kProjBlock, smem, s>>>(p);
+    k_project_bwd<DEG, ONE_VIEW><<<div_up(p.g.n, kProjBwdBlock), kProjBwdBlock, smem, s>>>(p);
     return cudaGetLastError();
 }
 
