@@ -147,6 +147,27 @@ def test_gradients_against_fp64_adjoint(cuda_ok):
         assert bad.mean() < 2e-3, (k, report[k])
 
 
+@pytest.mark.parametrize("tile,batch,persistent", [((8, 8), 32, True), ((32, 8), 128, False),
+                                                    ((32, 8), 512, True), ((16, 16), 64, False)])
+def test_gradients_other_tiles_and_batches(cuda_ok, tile, batch, persistent):
+    """The adjoint in every tile shape the autotuner may pick, with batches that split
+    each list into several staged rounds, per-tile and persistent launches."""
+    rng = np.random.default_rng(33)
+    sc = scenes.scene_uniform(rng, 900, [-1.4, -0.9, 2.5], [1.4, 0.9, 6], -3.3, 0.5, 1.5, 2)
+    cams = [scenes.identity_camera(150, 90, 85.0, 75.0, 45.0, bg=(0.2, 0.1, 0.3))]
+    ref = oracle.render(sc, cams[0], tile=tile)
+    dL = masked_upstream(scenes.upstream_grad(104, cams), [ref])
+    out = gpu_render(sc, cams, tile=tile, batch=batch, persistent=persistent, dL=dL)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    gref = oracle.render_bwd(sc, cams[0], dL[0], tile=tile, proj=ref["proj"], bins=ref["bins"])
+    vis = ref["proj"]["mode"] == oracle.NORMAL
+    bad, _ = grad_close(out["grad2d"][0][vis], gref["grad2d"][vis])
+    assert bad.mean() < 2e-3, f"grad2d: {bad.sum()} of {bad.size}"
+    for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
+        bad, _ = grad_close(out["grads"][k], gref[k])
+        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
+
+
 def test_multiview_persistent_matches_per_tile_launch(cuda_ok):
     rng = np.random.default_rng(41)
     sc = scenes.scene_uniform(rng, 3000, [-2, -2, -2], [2, 2, 2], -3.5, 0.6, 1.5, 2)
