@@ -22,8 +22,12 @@
 // Each warp owns an 8x4 block of the tile's pixels.  Per 32 staged splats it
 // tests every splat's cut-off ellipse (the pixels where alpha could reach 1/255)
 // against its block with separating axes (x, y and the ellipse's minor axis) and
-// ballots; only the hits are visited.  The bounds are inflated past the cut-off,
-// so culling changes no per-pixel decision.
+// ballots; only the hits are visited.  In the forward each 4x4 half of the block is
+// tested and walks its own hits, the two halves in step: a warp then takes as many
+// steps as the busier half has hits instead of one per hit of either half (0.77 of
+// them at 3M splats, 1080p; forward 0.676 -> 0.652 ms).  The backward keeps the
+// whole-block walk: the same split there cost 1.32 -> 1.40 ms.  The bounds are
+// inflated past the cut-off, so culling changes no per-pixel decision.
 //
 // The backward walks each pixel's list back to front from its last composited
 // splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i).
@@ -100,11 +104,12 @@ struct Batch {
 // numbers and stay exact to ~1e-7 px anywhere in the image.
 //
 // Culling data: the cut-off set E = {d : |U~ d|^2 <= qcut} has support function
-// h(n) = sqrt(qcut) |U~^-T n| in any unit direction n.  A warp's 8x4 block (pixel
-// centres within +-3.5, +-1.5 of its centre c) can touch E only if, for n = x, y and
-// n = the ellipse's minor axis, |n.(c - mu)| <= h(n) + 3.5|n_x| + 1.5|n_y|.  Every
-// bound is inflated (x1.001 + 1e-3) so that no block whose pixels pass the FP32
-// cut-off test of eval_alpha is culled.
+// h(n) = sqrt(qcut) |U~^-T n| in any unit direction n.  A block of pixels whose centres
+// lie within +-ex, +-1.5 of its centre c (the backward's 8x4 warp block, ex = 3.5; the
+// forward's 4x4 half-warp block, ex = 1.5) can touch E only if, for n = x, y and n = the
+// ellipse's minor axis, |n.(c - mu)| <= h(n) + ex|n_x| + 1.5|n_y|.  Every bound is
+// inflated (x1.001 + 1e-3) so that no block whose pixels pass the FP32 cut-off test of
+// eval_alpha is culled.
 template <int BATCH, bool BWD>
 __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t id, Batch<BATCH, BWD> &s, int k,
                                       float ox, float oy, bool plain) {
@@ -157,20 +162,34 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ rec, uint32_t i
         const float z1 = nx * i11;
         const float z2 = (ny - u12 * z1) * i22;
         const float hn = rq * sqrt_approx(z1 * z1 + z2 * z2);
-        const float tn = hn * 1.001f + 1e-3f + (fabsf(nx) * 3.5f + fabsf(ny) * 1.5f) * 1.0001f;
+        constexpr float ex = BWD ? 3.5f : 1.5f;     // block half-extents: 8x4 backward, 4x4 forward
+        const float tn = hn * 1.001f + 1e-3f + (fabsf(nx) * ex + fabsf(ny) * 1.5f) * 1.0001f;
         const float itn = rcp_approx(tn);
-        cu = make_float4(hx * 1.001f + 1e-3f + 3.5f, hy * 1.001f + 1e-3f + 1.5f, nx * itn, ny * itn);
+        cu = make_float4(hx * 1.001f + 1e-3f + ex, hy * 1.001f + 1e-3f + 1.5f, nx * itn, ny * itn);
     }
     s.cu[k] = cu;
 }
 
-// Can slot j touch the 8x4 block centred at (cx, cy)?  (conservative, see stage)
+// Backward: can slot j touch the 8x4 block centred at (cx, cy)?  (conservative, see stage)
 template <class SB>
 __device__ __forceinline__ bool cull_hit(const SB &s, int j, float cx, float cy) {
     const float2 m = *reinterpret_cast<const float2 *>(&s.g0[j]);
     const float4 cu = s.cu[j];
     const float dx = cx - m.x, dy = cy - m.y;
     return fabsf(dx) <= cu.x && fabsf(dy) <= cu.y && fabsf(__fmaf_rn(dx, cu.z, dy * cu.w)) <= 1.0f;
+}
+
+// Forward: can slot j touch the 4x4 blocks centred at (cx, cy) (h0) and (cx + 4, cy) (h1), the
+// two halves of a warp's 8x4 block?  (conservative, see stage)
+template <class SB>
+__device__ __forceinline__ void cull_halves(const SB &s, int j, float cx, float cy, bool &h0, bool &h1) {
+    const float2 m = *reinterpret_cast<const float2 *>(&s.g0[j]);
+    const float4 cu = s.cu[j];
+    const float dx0 = cx - m.x, dx1 = (cx + 4.0f) - m.x, dy = cy - m.y;
+    const float ty = dy * cu.w;
+    const bool yok = fabsf(dy) <= cu.y;
+    h0 = yok && fabsf(dx0) <= cu.x && fabsf(__fmaf_rn(dx0, cu.z, ty)) <= 1.0f;
+    h1 = yok && fabsf(dx1) <= cu.x && fabsf(__fmaf_rn(dx1, cu.z, ty)) <= 1.0f;
 }
 
 struct Eval {
@@ -281,13 +300,14 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
     const TileInfo ti = tile_info<TW, TH>(p, gtile);
     int bx, by;
     warp_block<TW>(ti, TH, part * (TH / SPLIT), bx, by);
-    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const int half = lane >> 4;             // 4x4 half of the warp's 8x4 block
+    const int px = bx + 4 * half + (lane & 3), py = by + ((lane >> 2) & 3);
     const bool inside = px < ti.W && py < ti.H;
     // tile-local coordinates (pixel centres at i + 1/2)
     const int ox = ti.tx * TW, oy = ti.ty * TH;
     const float fox = (float)ox, foy = (float)oy;
     const float fpx = (float)(px - ox) + 0.5f, fpy = (float)(py - oy) + 0.5f;
-    const float cxb = (float)(bx - ox) + 4.0f, cyb = (float)(by - oy) + 2.0f;   // block centre
+    const float cxb = (float)(bx - ox) + 2.0f, cyb = (float)(by - oy) + 2.0f;   // left half's centre
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
     const bool plain = p.cfg.plain != 0;
@@ -310,7 +330,11 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
         bool wdone = __all_sync(0xffffffffu, done);
         for (int c = 0; c < cnt && !wdone; c += 32) {
             const int jl = c + lane;
-            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && cull_hit(s, jl, cxb, cyb));
+            bool h0 = false, h1 = false;
+            if (jl < cnt) cull_halves(s, jl, cxb, cyb, h0, h1);
+            const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+            // each half walks its own hits, the two in step
+            unsigned m = half ? m1 : m0;
             while (m) {
                 const int k = c + __ffs(m) - 1;
                 m &= m - 1;
