@@ -451,12 +451,12 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
             }
         }
         __syncthreads();
-        const int cnt = (int)(bend - bstart);
         const uint32_t rel0 = bstart - ti.beg;
+        // this warp's part of the batch: nothing at or past its pixels' last splat
+        const int cnt = (int)min(bend - bstart, wlast > rel0 ? wlast - rel0 : 0u);
         for (int c = (cnt - 1) & ~31; c >= 0; c -= 32) {
             const int jl = c + lane;
-            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && rel0 + jl < wlast &&
-                                                        cull_hit(s, jl, cxb, cyb));
+            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && cull_hit(s, jl, cxb, cyb));
             while (m) {
                 const int bit = 31 - __clz(m);
                 m &= ~(1u << bit);
