@@ -472,8 +472,6 @@ __device__ __forceinline__ void camera_centre(const hgs_camera &cam, float c[3])
 // that 128-bit reads of consecutive threads fall in distinct banks.
 constexpr int kShStride3 = 52;
 
-__device__ __forceinline__ int sh_stride(int deg) { return deg == 3 ? kShStride3 : 3 * (deg + 1) * (deg + 1); }
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
@@ -501,6 +499,7 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int ro
 
 template <int NB>
 struct StageSmemN {
+    static constexpr int kRows = NB;
     float mean[3 * NB];
     float scale[3 * NB];
     float nrm[3 * NB];
@@ -520,11 +519,31 @@ using BwdStageSmem = StageSmemN<kProjBwdBlock>;
 // projection 0.219 vs 0.232 ms.  (Copying each thread's own row instead, so that no
 // barrier is needed, was slower: 0.246 ms; so was the adjoint restructured around the
 // barrier, hence it stages everything first.)
-template <class SM>
+// SH rows of degree DEG into shared memory at their padded stride.  The row width and
+// the block size are compile-time constants, so each 16-byte piece's row and column come
+// from a multiply-shift rather than a division (measured: the division made the
+// projection issue-bound at ~1,570 instructions per splat).
+template <int DEG, int NB>
+__device__ __forceinline__ void stage_sh(const float *__restrict__ src, int rows, float *dst) {
+    constexpr int nc3 = 3 * (DEG + 1) * (DEG + 1), shs = DEG == 3 ? kShStride3 : nc3;
+    if constexpr (nc3 == shs) {
+        stage_rows(src, rows, nc3, dst, nc3);
+    } else {                                   // nc3 is a multiple of 4
+        constexpr int per = nc3 / 4;
+        const int n4 = rows * per;
+#pragma unroll 4
+        for (int j = threadIdx.x; j < n4; j += NB) {
+            const int r = j / per, c = j - r * per;
+            cp_async16(dst + r * shs + 4 * c, src + (size_t)r * nc3 + 4 * c);
+        }
+    }
+}
+
+template <int DEG, class SM>
 __device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, int rows, SM &sm,
                                              const float *extra = nullptr, int extra_floats = 0,
                                              float *extra_dst = nullptr, bool sh_later = false) {
-    const int deg = g.sh_degree, nc3 = 3 * (deg + 1) * (deg + 1);
+    constexpr int nc3 = 3 * (DEG + 1) * (DEG + 1);
     if (extra) stage_rows(extra + (size_t)extra_floats * base, rows, extra_floats, extra_dst, extra_floats);
     stage_rows(g.means + 3 * (size_t)base, rows, 3, sm.mean, 3);
     stage_rows(g.scales + 3 * (size_t)base, rows, 3, sm.scale, 3);
@@ -534,11 +553,11 @@ __device__ __forceinline__ void stage_params(const hgs_gaussians &g, int base, i
     stage_rows(g.opac2 + base, rows, 1, sm.o2, 1);
     if (sh_later) {
         cp_async_commit();
-        stage_rows(g.sh + (size_t)nc3 * base, rows, nc3, sm.sh, sh_stride(deg));
+        stage_sh<DEG, SM::kRows>(g.sh + (size_t)nc3 * base, rows, sm.sh);
         cp_async_commit();
         cp_async_wait_prev();
     } else {
-        stage_rows(g.sh + (size_t)nc3 * base, rows, nc3, sm.sh, sh_stride(deg));
+        stage_sh<DEG, SM::kRows>(g.sh + (size_t)nc3 * base, rows, sm.sh);
         cp_async_wait_all();
     }
     __syncthreads();
@@ -746,7 +765,7 @@ __global__ void __launch_bounds__(kProjBlock, 5) k_project(ProjLaunch p) {
     const int n = p.g.n;
     const int base = blockIdx.x * kProjBlock;
     const int rows = min(kProjBlock, n - base);
-    stage_params(p.g, base, rows, sm, nullptr, 0, nullptr, ONE_VIEW);
+    stage_params<DEG>(p.g, base, rows, sm, nullptr, 0, nullptr, ONE_VIEW);
     const int t = threadIdx.x;
     const bool live = t < rows;
     const int i = base + t;
@@ -939,9 +958,9 @@ __global__ void __launch_bounds__(kProjBwdBlock, 8) k_project_bwd(ProjBwdLaunch 
     if (!ONE_VIEW)
         for (int j = threadIdx.x; j < kProjBwdBlock * shs; j += blockDim.x) gsh_s[j] = 0.0f;
     if (ONE_VIEW)
-        stage_params(p.g, base, rows, sm, p.grad2d, 12, extra);
+        stage_params<DEG>(p.g, base, rows, sm, p.grad2d, 12, extra);
     else
-        stage_params(p.g, base, rows, sm);
+        stage_params<DEG>(p.g, base, rows, sm);
     const int t = threadIdx.x;
     const float lp = p.cfg.lowpass;
     float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gn[3] = {0, 0, 0};
