@@ -47,6 +47,27 @@ __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); 
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 
+// Reciprocal and square root of the free-order terms (the conic factor, the half-plane
+// terms and the adjoint): the PTX approximations in FP32 (relative error ~1e-7, far
+// inside the FP32 parity bars, one instruction instead of an IEEE sequence), the exact
+// operations in FP64.  The binning fields never use them.
+template <typename T>
+__device__ __forceinline__ T rcp_f(T x) { return (T)1 / x; }
+template <>
+__device__ __forceinline__ float rcp_f<float>(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <typename T>
+__device__ __forceinline__ T sqrt_f(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float sqrt_f<float>(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---- compensated binary32 arithmetic (value = hi + lo) ---------------------------
 // Used for the projected centre, which must be exact to ~1e-7 px although it is
 // near 2000 px: t = W mu + t_c, x/z and f x/z + c are formed from error-free
@@ -316,8 +337,8 @@ struct Proj {
                                         const float *nrm, const hgs_camera &cam, float lp,
                                         int fov_clamp) {
         const float *V = cam.viewmat;
-        qn = sqrt((T)q[0] * q[0] + (T)q[1] * q[1] + (T)q[2] * q[2] + (T)q[3] * q[3]);
-        T iq = (T)1 / qn;
+        qn = sqrt_f((T)q[0] * q[0] + (T)q[1] * q[1] + (T)q[2] * q[2] + (T)q[3] * q[3]);
+        T iq = rcp_f(qn);
 #pragma unroll
         for (int i = 0; i < 4; ++i) qh[i] = (T)q[i] * iq;
         const T a0 = qh[0], a1 = qh[1], a2 = qh[2], a3 = qh[3];   // (w, x, y, z)
@@ -331,18 +352,19 @@ struct Proj {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
             t[i] = (T)V[4 * i] * m[0] + (T)V[4 * i + 1] * m[1] + (T)V[4 * i + 2] * m[2] + (T)V[4 * i + 3];
-        T ux = t[0] / t[2], uy = t[1] / t[2];
+        const T itz = rcp_f(t[2]);
+        T ux = t[0] * itz, uy = t[1] * itz;
         uxc = ux; uyc = uy; clx = cly = false;
         if (fov_clamp) {
-            T limx = (T)1.3 * ((T)0.5 * cam.width / (T)cam.fx);
-            T limy = (T)1.3 * ((T)0.5 * cam.height / (T)cam.fy);
+            T limx = (T)1.3 * ((T)0.5 * cam.width * rcp_f((T)cam.fx));
+            T limy = (T)1.3 * ((T)0.5 * cam.height * rcp_f((T)cam.fy));
             if (ux > limx) { uxc = limx; clx = true; }
             if (ux < -limx) { uxc = -limx; clx = true; }
             if (uy > limy) { uyc = limy; cly = true; }
             if (uy < -limy) { uyc = -limy; cly = true; }
         }
-        J00 = (T)cam.fx / t[2]; J02 = -(T)cam.fx * uxc / t[2];
-        J11 = (T)cam.fy / t[2]; J12 = -(T)cam.fy * uyc / t[2];
+        J00 = (T)cam.fx * itz; J02 = -(T)cam.fx * uxc * itz;
+        J11 = (T)cam.fy * itz; J12 = -(T)cam.fy * uyc * itz;
 #pragma unroll
         for (int kk = 0; kk < 3; ++kk) {
             M[0][kk] = J00 * V[kk] + J02 * V[8 + kk];
@@ -361,13 +383,13 @@ struct Proj {
         cross3(P[0], P[1], cr);
         det0 = dot3(cr, cr);
         det = det0 + (T)lp * (n0 + n1) + (T)lp * (T)lp;
-        T id = (T)1 / det;
+        T id = rcp_f(det);
         Q[0] = c * id; Q[1] = -b * id; Q[2] = a * id;
-        nn = sqrt((T)nrm[0] * nrm[0] + (T)nrm[1] * nrm[1] + (T)nrm[2] * nrm[2]);
+        nn = sqrt_f((T)nrm[0] * nrm[0] + (T)nrm[1] * nrm[1] + (T)nrm[2] * nrm[2]);
         var_s = v = 0; k[0] = k[1] = w[0] = w[1] = 0;
         u[0] = u[1] = u[2] = nh[0] = nh[1] = nh[2] = 0;
         if (nn < (T)1e-12) { mode = MODE_HALF; return; }
-        T in = (T)1 / nn;
+        T in = rcp_f(nn);
 #pragma unroll
         for (int i = 0; i < 3; ++i) nh[i] = (T)nrm[i] * in;
 #pragma unroll
@@ -390,7 +412,7 @@ struct Proj {
     }
 
     // Opacity factor of the Mip-Splatting 2D filter: sqrt(det hat Sigma_0 / det hat Sigma).
-    __device__ __forceinline__ T mip_factor() const { return det0 > (T)0 ? sqrt(det0 / det) : (T)0; }
+    __device__ __forceinline__ T mip_factor() const { return det0 > (T)0 ? sqrt_f(det0 * rcp_f(det)) : (T)0; }
 };
 
 // ---- real spherical harmonics, degree <= 3 ---------------------------------
@@ -695,21 +717,22 @@ __device__ __forceinline__ bool project_geo(const ProjLaunch &p, const Params &P
     cross3(cb.P[0], cb.P[1], cr);
     const float det0 = dot3(cr, cr);
     const float det = det0 + lp * (n0 + n1) + lp * lp;
+    const float id = rcp_f(det);
     const float a_ = cb.a, b_ = cb.b, c_ = cb.c;
     out.wpx = out.wpy = 0.0f;
     // Mip-Splatting's 2D filter: the low-pass as a normalised convolution scales the
-    // footprint by sqrt(det hat Sigma_0 / det hat Sigma), both halves alike
+    // footprint by sqrt(det hat Sigma_0 / det hat Sigma), both halves alike (exact
+    // operations: with no low-pass the factor is exactly 1)
     out.comp = p.cfg.mip ? sqrtf(det0 / det) : 1.0f;
-    const float nn = sqrtf(dot3(P.n, P.n));
+    const float nn = sqrt_f(dot3(P.n, P.n));
     if (nn >= 1e-12f) {
-        const float in = 1.0f / nn;
+        const float in = rcp_f(nn);
         const float nh[3] = {P.n[0] * in, P.n[1] * in, P.n[2] * in};
         float u[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) u[k] = cb.L[0][k] * nh[0] + cb.L[1][k] * nh[1] + cb.L[2][k] * nh[2];
         const float var_s = dot3(u, u);
         const float k0 = dot3(cb.P[0], u), k1 = dot3(cb.P[1], u);
-        const float id = 1.0f / det;
         const float wx = (c_ * k0 - b_ * k1) * id;
         const float wy = (a_ * k1 - b_ * k0) * id;
         float up0[3], up1[3];
@@ -727,7 +750,7 @@ __device__ __forceinline__ bool project_geo(const ProjLaunch &p, const Params &P
     }
     // Cholesky factor of the conic
     out.u22 = rsqrtf(c_);
-    out.u11 = sqrtf(c_ / det);
+    out.u11 = sqrt_f(c_ * id);
     out.u12 = -b_ * rsqrtf(c_ * det);
     list_append(p.out.fp64_list, defer, (uint32_t)vi);
     return true;
@@ -822,7 +845,7 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
     T gA = g2[2], gB = g2[3], gC = g2[4];
     T gk[2] = {0, 0}, gvar = 0;
     if (f.mode == MODE_NORMAL) {
-        T sv = (T)1 / sqrt((T)2 * f.v);
+        T sv = rcp_f(sqrt_f((T)2 * f.v));
         T gw0 = (T)g2[5] * sv, gw1 = (T)g2[6] * sv;
         T gv = -((T)g2[5] * f.w[0] + (T)g2[6] * f.w[1]) * sv * sv * sv;
         gvar = gv;
@@ -842,7 +865,7 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
     // comp = sqrt(det hat Sigma_0 / det hat Sigma):
     // d comp = comp/2 tr((hat Sigma_0^-1 - hat Sigma^-1) d hat Sigma_0), d hat Sigma = d hat Sigma_0
     if (g_comp != (T)0 && f.det0 > (T)0) {
-        const T h = (T)0.5 * g_comp * f.mip_factor(), i0 = (T)1 / f.det0;
+        const T h = (T)0.5 * g_comp * f.mip_factor(), i0 = rcp_f(f.det0);
         Gs00 += h * (f.n1 * i0 - f.Q[0]);
         Gs01 += h * (-f.b * i0 - f.Q[1]);
         Gs11 += h * (f.n0 * i0 - f.Q[2]);
@@ -872,7 +895,7 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
         for (int j = 0; j < 3; ++j) gnh[j] = f.L[j][0] * gu[0] + f.L[j][1] * gu[1] + f.L[j][2] * gu[2];
         T dd = gnh[0] * f.nh[0] + gnh[1] * f.nh[1] + gnh[2] * f.nh[2];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) gn[j] += (float)((gnh[j] - dd * f.nh[j]) / f.nn);
+        for (int j = 0; j < 3; ++j) gn[j] += (float)((gnh[j] - dd * f.nh[j]) * rcp_f(f.nn));
     }
     // L = R diag(s)
     T gR[3][3];
@@ -898,13 +921,13 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
                   x * gR[2][0] + y * gR[2][1]);
     T dq = gqh[0] * w + gqh[1] * x + gqh[2] * y + gqh[3] * z;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) gq[j] += (float)((gqh[j] - dq * f.qh[j]) / f.qn);
+    for (int j = 0; j < 4; ++j) gq[j] += (float)((gqh[j] - dq * f.qh[j]) * rcp_f(f.qn));
     // M = J W
     T gJ00 = gM[0][0] * V[0] + gM[0][1] * V[1] + gM[0][2] * V[2];
     T gJ02 = gM[0][0] * V[8] + gM[0][1] * V[9] + gM[0][2] * V[10];
     T gJ11 = gM[1][0] * V[4] + gM[1][1] * V[5] + gM[1][2] * V[6];
     T gJ12 = gM[1][0] * V[8] + gM[1][1] * V[9] + gM[1][2] * V[10];
-    T tz = f.t[2], itz = (T)1 / tz, itz2 = itz * itz;
+    T tz = f.t[2], itz = rcp_f(tz), itz2 = itz * itz;
     T fx = cam.fx, fy = cam.fy;
     T gt[3] = {0, 0, 0};
     gt[2] -= (gJ00 * fx + gJ11 * fy) * itz2;
