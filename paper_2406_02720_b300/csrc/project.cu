@@ -48,7 +48,7 @@ __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 
 // Reciprocal and square root of the free-order terms (the conic factor, the half-plane
-// terms and the adjoint): the PTX approximations in FP32 (relative error ~1e-7, far
+// terms, the compensated centre's first quotient and the adjoint): the PTX approximations in FP32 (relative error ~1e-7, far
 // inside the FP32 parity bars, one instruction instead of an IEEE sequence), the exact
 // operations in FP64.  The binning fields never use them.
 template <typename T>
@@ -96,14 +96,18 @@ __device__ __forceinline__ DF df_mul(DF a, float b) {
     const DF p = two_prod(a.hi, b);
     return df_renorm(p.hi, __fmaf_rn(a.lo, b, p.lo));
 }
-__device__ __forceinline__ DF df_div(DF a, DF b) {
-    const float q1 = __fdiv_rn(a.hi, b.hi);
+// a / b with ib ~ 1 / b.hi (a few ulp): the first quotient q1 = a.hi ib, then the
+// residual a - q1 b, formed exactly from an error-free product, times ib.  The residual
+// absorbs q1's error, so the pair is accurate to ~1e-7 of the residual, far below an ulp
+// of q1.
+__device__ __forceinline__ DF df_div(DF a, DF b, float ib) {
+    const float q1 = __fmul_rn(a.hi, ib);
     const DF p = two_prod(q1, b.hi);
     float r = __fsub_rn(a.hi, p.hi);
     r = __fsub_rn(r, p.lo);
     r = __fadd_rn(r, a.lo);
     r = __fsub_rn(r, __fmul_rn(q1, b.lo));
-    return df_renorm(q1, __fdiv_rn(r, b.hi));
+    return df_renorm(q1, __fmul_rn(r, ib));
 }
 
 // Projected centre (anchor = nearest integer, fraction = rest), compensated.
@@ -117,8 +121,9 @@ __device__ __forceinline__ void precise_centre(const float m[3], const hgs_camer
         acc = df_add(acc, two_prod(V[4 * i + 2], m[2]));
         t[i] = df_add(acc, DF{V[4 * i + 3], 0.0f});
     }
-    const DF mx = df_add(df_mul(df_div(t[0], t[2]), cam.fx), DF{cam.cx, 0.0f});
-    const DF my = df_add(df_mul(df_div(t[1], t[2]), cam.fy), DF{cam.cy, 0.0f});
+    const float iz = rcp_f(t[2].hi);
+    const DF mx = df_add(df_mul(df_div(t[0], t[2], iz), cam.fx), DF{cam.cx, 0.0f});
+    const DF my = df_add(df_mul(df_div(t[1], t[2], iz), cam.fy), DF{cam.cy, 0.0f});
     out[0] = rintf(mx.hi);
     out[1] = rintf(my.hi);
     out[2] = __fadd_rn(__fsub_rn(mx.hi, out[0]), mx.lo);
