@@ -59,10 +59,13 @@ def lib():
         L.or_bin.restype = c_long
         L.or_render_fwd.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, POINTER(c_uint32),
                                     POINTER(c_uint32), POINTER(OrCamera), POINTER(OrOpts),
-                                    POINTER(c_ubyte), dp, dp, ip, dp, dp, dp, ip]
+                                    POINTER(c_ubyte), dp, dp, ip, dp, dp, dp, ip,
+                                    dp, dp, dp, dp, POINTER(c_ubyte)]
+        L.or_error_basis.argtypes = [c_int, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts), ip,
+                                     POINTER(c_ubyte), dp, dp]
         L.or_render_bwd.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, POINTER(c_uint32),
                                     POINTER(c_uint32), POINTER(OrCamera), POINTER(OrOpts),
-                                    POINTER(c_ubyte), dp, dp]
+                                    POINTER(c_ubyte), dp, dp, dp, dp]
         L.or_project_bwd.argtypes = [c_int, dp, dp, dp, dp, dp, dp, dp, POINTER(OrCamera),
                                      POINTER(OrOpts), ip, dp, dp, dp, dp, dp, dp, dp, dp]
         L.or_eval_splat.argtypes = [dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts), c_int,
@@ -90,12 +93,15 @@ def make_camera(cam) -> OrCamera:
     vm = np.asarray(cam.viewmat, np.float64).reshape(12)
     for i in range(12):
         c.viewmat[i] = float(vm[i])
-    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    # the camera of the C ABI is binary32 (hgs_camera): take the same binary32 values
+    # for the intrinsics, the near plane and the background as for the view matrix
+    f32 = lambda x: float(np.float32(x))      # noqa: E731
+    c.fx, c.fy, c.cx, c.cy = f32(cam.fx), f32(cam.fy), f32(cam.cx), f32(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
-    c.near_plane = float(getattr(cam, "near", 0.2))
+    c.near_plane = f32(getattr(cam, "near", 0.2))
     bg = getattr(cam, "bg", (0.0, 0.0, 0.0))
     for i in range(3):
-        c.bg[i] = float(bg[i])
+        c.bg[i] = f32(bg[i])
     return c
 
 
@@ -126,11 +132,14 @@ def grid(cam, tile):
     return tx, ty
 
 
-def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0, mip=False):
+def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0, mip=False, errmat=True,
+            err_sel=None):
     """Per-splat projection (Eq. 2-5, 7-8; SH colour), plus canonical binning fields.
     rect_mode 0: the 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4).
     mip: the low-pass as Mip-Splatting's mass-preserving 2D filter; "opac1"/"opac2" are
-    then the compensated opacities the compositing uses ("comp" holds the factor)."""
+    then the compensated opacities the compositing uses ("comp" holds the factor).
+    errmat: also the FP32 error model's per-splat matrix "errmat" [N,15] (see
+    error_basis), for the splats selected by err_sel [N] bool (all if None)."""
     s = _scene64(sc)
     n = s["means"].shape[0]
     o = make_opts(tile, sc.sh_degree, lowpass, False, fov_clamp, rect_mode, mip)
@@ -149,7 +158,33 @@ def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0, mi
                      _p(out["canon_mu"], fp), _p(out["mu2"], dp), _p(out["conic"], dp),
                      _p(out["wp"], dp), _p(out["rgb"], dp), _p(out["var_terms"], dp), _p(out["comp"], dp))
     out["opac1"], out["opac2"] = s["opac1"] * out["comp"], s["opac2"] * out["comp"]
+    if errmat:
+        out["errmat"] = error_basis(sc, cam, out["mode"], lowpass=lowpass, fov_clamp=fov_clamp, sel=err_sel,
+                                    scene64=s)
     return out
+
+
+def error_basis(sc, cam, mode, lowpass=0.3, fov_clamp=True, sel=None, scene64=None, vectors=False):
+    """FP32 error model, shape part: per splat, E = sum_k v_k v_k^T over the 22 inputs of
+    the shape terms y = (conic A, B, C, w'x, w'y) (camera-space mean, camera rotation,
+    scales, raw quaternion, raw normal), v_k = |x_k| dy/dx_k by central differences in
+    FP64: the change of y per unit relative perturbation of x_k.  Returns E [N,15]
+    (upper triangle row by row), and with vectors=True also V [N,22,5]."""
+    s = scene64 if scene64 is not None else _scene64(sc)
+    n = s["means"].shape[0]
+    o = make_opts((16, 16), sc.sh_degree, lowpass, False, fov_clamp)
+    c = make_camera(cam)
+    E = np.zeros((n, 15))
+    V = np.zeros((n, 22, 5)) if vectors else None
+    mode = np.ascontiguousarray(mode, np.int32)
+    selp = None
+    if sel is not None:
+        sel = np.ascontiguousarray(np.asarray(sel).astype(np.uint8).reshape(n))
+        selp = _p(sel, c_ubyte)
+    lib().or_error_basis(n, _p(s["means"], c_double), _p(s["scales"], c_double), _p(s["quats"], c_double),
+                         _p(s["normals"], c_double), ctypes.byref(c), ctypes.byref(o), _p(mode, c_int), selp,
+                         _p(E, c_double), _p(V, c_double) if vectors else None)
+    return (E, V) if vectors else E
 
 
 def bin_pairs(proj, cam, tile=(16, 16), tile_mask=None):
@@ -185,15 +220,20 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     """Forward image: front-to-back compositing of the Eq. 10 pair weights over each
     tile's depth-sorted list (3-sigma tile culling, 1/255 floor, 0.99 clamp, 1e-4 stop).
 
-    Returns image [3,H,W], T [H,W], n_contrib [H,W], margin [H,W] (FP64; also split
-    into margin_a for the 1/255 floor and margin_T for the 1e-4 stop, with n_comp the
-    number of composited splats) and the projection/binning intermediates."""
+    Returns image [3,H,W], T [H,W], n_contrib [H,W], margin [H,W] (the smallest relative
+    distance of a decision to its threshold), n_comp (composited splats), the
+    intermediates proj/bins, and the FP32 error model's verdicts (reading B15):
+    margin_a (1/255 floor and step sign), margin_T (1e-4 stop), margin_c (0.99 clamp),
+    each the distance to the threshold over the error a binary32 evaluation can carry
+    there (<= 1: FP32 cannot be expected to decide it as FP64 does); flip_img, flip_T:
+    how far those decisions can move the pixel; touched [N]: splats with such a
+    decision in some pixel."""
     if proj is None:
         proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     W, H = int(cam.width), int(cam.height)
-    o = make_opts(tile, sc.sh_degree, lowpass, plain, fov_clamp)
+    o = make_opts(tile, sc.sh_degree, lowpass, plain, fov_clamp, mip=mip)
     c = make_camera(cam)
     image = np.zeros((3, H, W))
     T = np.zeros((H, W))
@@ -202,6 +242,15 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     mga = np.full((H, W), np.inf)
     mgT = np.full((H, W), np.inf)
     ncomp = np.zeros((H, W), np.int32)
+    mgc = np.full((H, W), np.inf)
+    flip_img = np.zeros((H, W))
+    flip_T = np.zeros((H, W))
+    n = proj["mode"].shape[0]
+    touched = np.zeros(n, np.uint8)
+    em = proj.get("errmat")
+    if em is not None:
+        em = np.ascontiguousarray(em, np.float64)      # kept alive across the call
+    em_p = _p(em, c_double) if em is not None else None
     mask_p = None
     if tile_mask is not None:
         tile_mask = np.ascontiguousarray(tile_mask, dtype=np.uint8)
@@ -215,24 +264,32 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
                         _p(proj["opac1"], dp), _p(proj["opac2"], dp), _p(ids, c_uint32),
                         _p(bins["ranges"], c_uint32), ctypes.byref(c), ctypes.byref(o), mask_p,
                         _p(image, dp), _p(T, dp), _p(nc, c_int), _p(mg, dp), _p(mga, dp), _p(mgT, dp),
-                        _p(ncomp, c_int))
-    return dict(image=image, T=T, n_contrib=nc, margin=mg, margin_a=mga, margin_T=mgT, n_comp=ncomp,
+                        _p(ncomp, c_int), em_p, _p(mgc, dp), _p(flip_img, dp), _p(flip_T, dp),
+                        _p(touched, c_ubyte))
+    return dict(image=image, T=T, n_contrib=nc, margin=mg, margin_a=mga, margin_T=mgT, margin_c=mgc,
+                n_comp=ncomp, flip_img=flip_img, flip_T=flip_T, touched=touched.astype(bool),
                 proj=proj, bins=bins)
 
 
 def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
-                  tile_mask=None, proj=None, bins=None, mip=False):
+                  tile_mask=None, proj=None, bins=None, mip=False, with_err=False):
     """FP64 adjoint of the compositing alone (Eq. 10 blending, back to front) for the
     loss L = sum(dL_dimage * image): the per-splat screen-space gradients grad2d
-    [N,12] (fields G2D_FIELDS; alpha1/alpha2 are the opacities the compositing used)."""
+    [N,12] (fields G2D_FIELDS; alpha1/alpha2 are the opacities the compositing used).
+    with_err: also the FP32 error model's first-order bound on each entry [N,12],
+    returned as (grad2d, grad2d_err)."""
     if proj is None:
         proj = project(sc, cam, tile, lowpass, fov_clamp, mip=mip)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     n = int(np.asarray(proj["mode"]).shape[0])
-    o = make_opts(tile, sc.sh_degree, lowpass, plain, fov_clamp)
+    o = make_opts(tile, sc.sh_degree, lowpass, plain, fov_clamp, mip=mip)
     c = make_camera(cam)
     g2 = np.zeros((n, 12))
+    g2e = np.zeros((n, 12)) if with_err else None
+    em = proj.get("errmat")
+    if em is not None:
+        em = np.ascontiguousarray(em, np.float64)
     mask_p = None
     if tile_mask is not None:
         tile_mask = np.ascontiguousarray(tile_mask, dtype=np.uint8)
@@ -245,8 +302,9 @@ def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, f
     lib().or_render_bwd(n, _p(proj["mode"], c_int), _p(proj["mu2"], dp), _p(proj["conic"], dp),
                         _p(proj["wp"], dp), _p(proj["rgb"], dp), _p(proj["opac1"], dp),
                         _p(proj["opac2"], dp), _p(ids, c_uint32), _p(bins["ranges"], c_uint32),
-                        ctypes.byref(c), ctypes.byref(o), mask_p, _p(dLd, dp), _p(g2, dp))
-    return g2
+                        ctypes.byref(c), ctypes.byref(o), mask_p, _p(dLd, dp), _p(g2, dp),
+                        _p(em, dp) if em is not None else None, _p(g2e, dp) if with_err else None)
+    return (g2, g2e) if with_err else g2
 
 
 def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,
@@ -259,10 +317,47 @@ def render_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_
         proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
-    g2 = rasterize_bwd(sc, cam, dL_dimage, tile, lowpass, plain, fov_clamp, tile_mask, proj, bins)
+    g2, g2e = rasterize_bwd(sc, cam, dL_dimage, tile, lowpass, plain, fov_clamp, tile_mask, proj, bins, mip,
+                            with_err=True)
     grads = project_bwd(sc, cam, proj["mode"], g2, tile, lowpass, fov_clamp, mip)
     grads["grad2d"] = g2
+    grads["grad2d_err"] = g2e
+    live = np.abs(g2).max(1) > 0
+    for k, v in param_error_bound(sc, cam, proj["mode"], g2, g2e, live, tile, lowpass, fov_clamp, mip).items():
+        grads["err_" + k] = v
     return grads
+
+
+# Relative rounding of a binary32 evaluation of the projection adjoint, per input: the
+# longest chain of rounded operations from one screen-space gradient entry to a
+# parameter gradient is about 32 operations deep.
+ADJ_EVAL_ULPS = 32.0
+U32 = 2.0 ** -24
+
+
+def param_error_bound(sc, cam, mode, grad2d, grad2d_err, live=None, tile=(16, 16), lowpass=0.3, fov_clamp=True,
+                      mip=False):
+    """First-order bound on the error of a binary32 evaluation of the parameter
+    gradients: |J|^T (grad2d_err + ADJ_EVAL_ULPS u |grad2d|) per splat, J the Jacobian
+    of the projection (parameters -> the 12 screen-space quantities), formed one
+    screen-space field at a time with this oracle's FP64 adjoint.  `live` (bool [N])
+    restricts the work to splats with a nonzero screen-space gradient."""
+    n = int(np.asarray(mode).shape[0])
+    m = np.asarray(mode, np.int32).copy()
+    if live is not None:
+        m[~np.asarray(live, bool)] = CULLED
+    x = np.abs(np.asarray(grad2d_err, np.float64)) + ADJ_EVAL_ULPS * U32 * np.abs(np.asarray(grad2d, np.float64))
+    out = None
+    for f in range(12):
+        e = np.zeros((n, 12))
+        e[:, f] = x[:, f]
+        g = project_bwd(sc, cam, m, e, tile, lowpass, fov_clamp, mip)
+        if out is None:
+            out = {k: np.abs(v) for k, v in g.items()}
+        else:
+            for k in out:
+                out[k] += np.abs(g[k])
+    return out
 
 
 def project_bwd(sc, cam, mode, grad2d, tile=(16, 16), lowpass=0.3, fov_clamp=True, mip=False):

@@ -62,7 +62,7 @@ enum { OR_CULLED = 0, OR_NORMAL = 1, OR_STEP = 2, OR_HALF = 3 };
 #define OR_ALPHA_MAX 0.99
 #define OR_T_MIN 1e-4
 
-int or_abi_version(void) { return 5; }
+int or_abi_version(void) { return 6; }
 
 int or_num_threads(void)
 {
@@ -509,6 +509,144 @@ static double half_fraction(const fwd_t *f, double dx, double dy, double *margin
 }
 
 /* ------------------------------------------------------------------------ */
+/* FP32 error model: how far a binary32 evaluation of the pair weight can      */
+/* be from the FP64 value.  It decides which threshold decisions of the       */
+/* compositing (1/255 floor, 0.99 clamp, 1e-4 stop, step sign) a binary32     */
+/* implementation cannot be expected to reproduce (reading B15).              */
+/*                                                                            */
+/* Shape part.  The screen-space shape terms y = (conic A, B, C, w'x, w'y)    */
+/* are modelled as computed backward-stably: the binary32 result is the exact */
+/* result for inputs each perturbed by a relative amount of the order of the  */
+/* unit roundoff.  The inputs are the 22 values that enter the shape: the     */
+/* camera-space mean t (3), the camera rotation (9), the scales (3), the raw  */
+/* quaternion (4) and the raw normal (3).  For each input x_k the vector      */
+/* v_k = |x_k| dy/dx_k (central differences in FP64) is the change of y per   */
+/* unit relative perturbation; E = sum_k v_k v_k^T combines the 22 as         */
+/* independent rounding errors (root-sum-square).  Splats whose plane nearly  */
+/* contains the ray (v < 1e-3 var_s) have their w' computed in FP64 by a      */
+/* binary32 implementation of this design, so only the final rounding of w'   */
+/* enters there.                                                              */
+/* ------------------------------------------------------------------------ */
+#define OR_ERR_DIRS 22
+#define OR_U32 5.9604644775390625e-8     /* 2^-24: unit roundoff of binary32       */
+#define OR_FP64_GATE 1e-3                /* v / var_s below which w' is FP64       */
+
+/* y = (A, B, C, w'x, w'y) from the inputs x (layout of error_basis_one); returns the
+ * mode and writes v / var_s (0 when there is no normal). */
+static int shape_terms(const double x[OR_ERR_DIRS], const or_camera *cam, const or_opts *o,
+                       double y[5], double *vrel)
+{
+    const double *t = x, *Rcf = x + 3, *scale = x + 12, *quat = x + 15, *normal = x + 19;
+    double qn = sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);
+    double qh[4] = {quat[0] / qn, quat[1] / qn, quat[2] / qn, quat[3] / qn};
+    double R[3][3], Sw[3][3];
+    quat_to_rot(qh, R);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += R[i][k] * scale[k] * scale[k] * R[j][k];
+            Sw[i][j] = acc;
+        }
+    double tz = t[2];
+    double uxc = t[0] / tz, uyc = t[1] / tz;
+    if (o->fov_clamp) {
+        double limx = 1.3 * (0.5 * cam->width / cam->fx);
+        double limy = 1.3 * (0.5 * cam->height / cam->fy);
+        uxc = fmin(fmax(uxc, -limx), limx);
+        uyc = fmin(fmax(uyc, -limy), limy);
+    }
+    double J00 = cam->fx / tz, J02 = -cam->fx * uxc / tz, J11 = cam->fy / tz, J12 = -cam->fy * uyc / tz;
+    double M[2][3];
+    for (int k = 0; k < 3; ++k) {
+        M[0][k] = J00 * Rcf[k] + J02 * Rcf[6 + k];
+        M[1][k] = J11 * Rcf[3 + k] + J12 * Rcf[6 + k];
+    }
+    double MS[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) MS[i][j] = M[i][0] * Sw[0][j] + M[i][1] * Sw[1][j] + M[i][2] * Sw[2][j];
+    double a = MS[0][0] * M[0][0] + MS[0][1] * M[0][1] + MS[0][2] * M[0][2] + o->lowpass;
+    double b = MS[0][0] * M[1][0] + MS[0][1] * M[1][1] + MS[0][2] * M[1][2];
+    double c = MS[1][0] * M[1][0] + MS[1][1] * M[1][1] + MS[1][2] * M[1][2] + o->lowpass;
+    double det = a * c - b * b;
+    y[0] = c / det; y[1] = -b / det; y[2] = a / det;
+    y[3] = y[4] = 0.0;
+    *vrel = 0.0;
+    double nn = sqrt(normal[0] * normal[0] + normal[1] * normal[1] + normal[2] * normal[2]);
+    if (nn < 1e-12) return OR_HALF;
+    double nh[3] = {normal[0] / nn, normal[1] / nn, normal[2] / nn}, Sn[3];
+    for (int i = 0; i < 3; ++i) Sn[i] = Sw[i][0] * nh[0] + Sw[i][1] * nh[1] + Sw[i][2] * nh[2];
+    double var_s = nh[0] * Sn[0] + nh[1] * Sn[1] + nh[2] * Sn[2];
+    double k0 = M[0][0] * Sn[0] + M[0][1] * Sn[1] + M[0][2] * Sn[2];
+    double k1 = M[1][0] * Sn[0] + M[1][1] * Sn[1] + M[1][2] * Sn[2];
+    double w0 = y[0] * k0 + y[1] * k1, w1 = y[1] * k0 + y[2] * k1;
+    double v = var_s - (k0 * w0 + k1 * w1);
+    *vrel = var_s > 0 ? v / var_s : 0.0;
+    if (v <= 1e-12 * var_s) return OR_STEP;
+    double sc = 1.0 / sqrt(2.0 * v);
+    y[3] = w0 * sc; y[4] = w1 * sc;
+    return OR_NORMAL;
+}
+
+/* The 22 unit-perturbation vectors v_k of one splat (V, optional) and E = sum v v^T
+ * (upper triangle, row by row: 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44). */
+static void error_basis_one(const double *mean, const double *scale, const double *quat,
+                            const double *normal, const or_camera *cam, const or_opts *o,
+                            double V[OR_ERR_DIRS][5], double E[15])
+{
+    const double *W = cam->viewmat;
+    double x[OR_ERR_DIRS];
+    for (int i = 0; i < 3; ++i) x[i] = W[4 * i] * mean[0] + W[4 * i + 1] * mean[1] + W[4 * i + 2] * mean[2] + W[4 * i + 3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) x[3 + 3 * i + j] = W[4 * i + j];
+    for (int k = 0; k < 3; ++k) x[12 + k] = scale[k];
+    for (int k = 0; k < 4; ++k) x[15 + k] = quat[k];
+    for (int k = 0; k < 3; ++k) x[19 + k] = normal[k];
+    double y0[5], vrel0, Vl[OR_ERR_DIRS][5];
+    int mode0 = shape_terms(x, cam, o, y0, &vrel0);
+    int fp64_w = mode0 != OR_NORMAL || vrel0 < OR_FP64_GATE;
+    for (int k = 0; k < OR_ERR_DIRS; ++k) {
+        for (int j = 0; j < 5; ++j) Vl[k][j] = 0.0;
+        if (x[k] == 0.0) continue;                 /* an exact zero stays exact */
+        double h = 1e-6 * fabs(x[k]), xp[OR_ERR_DIRS], xm[OR_ERR_DIRS], yp[5], ym[5], vr;
+        memcpy(xp, x, sizeof(x));
+        memcpy(xm, x, sizeof(x));
+        xp[k] += h;
+        xm[k] -= h;
+        shape_terms(xp, cam, o, yp, &vr);
+        shape_terms(xm, cam, o, ym, &vr);
+        for (int j = 0; j < (fp64_w ? 3 : 5); ++j) Vl[k][j] = (yp[j] - ym[j]) / (2.0 * h) * fabs(x[k]);
+    }
+    int q = 0;
+    for (int a = 0; a < 5; ++a)
+        for (int b = a; b < 5; ++b) {
+            double acc = 0;
+            for (int k = 0; k < OR_ERR_DIRS; ++k) acc += Vl[k][a] * Vl[k][b];
+            /* FP64 w' (gathered splats): its final rounding to binary32 only */
+            if (fp64_w && mode0 == OR_NORMAL && a >= 3 && b >= 3) acc += y0[a] * y0[b];
+            E[q++] = acc;
+        }
+    if (V) memcpy(V, Vl, sizeof(Vl));
+}
+
+/* E [n,15] for the splats with sel[i] != 0 (all when sel is NULL) that project (mode
+ * != OR_CULLED); zero rows elsewhere.  V (optional) [n,22,5]. */
+int or_error_basis(int n, const double *means, const double *scales, const double *quats,
+                   const double *normals, const or_camera *cam, const or_opts *o, const int *mode,
+                   const unsigned char *sel, double *E, double *V)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int i = 0; i < n; ++i) {
+        double *Ei = E + 15 * (size_t)i;
+        for (int j = 0; j < 15; ++j) Ei[j] = 0.0;
+        if (V) for (int j = 0; j < OR_ERR_DIRS * 5; ++j) V[(size_t)i * OR_ERR_DIRS * 5 + j] = 0.0;
+        if ((sel && !sel[i]) || mode[i] == OR_CULLED) continue;
+        error_basis_one(means + 3 * i, scales + 3 * i, quats + 4 * i, normals + 3 * i, cam, o,
+                        V ? (double (*)[5])(V + (size_t)i * OR_ERR_DIRS * 5) : NULL, Ei);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Projection of all splats: canonical binning fields + FP64 continuous ones. */
 /* ------------------------------------------------------------------------ */
 int or_project(int n, const double *means, const double *scales, const double *quats,
@@ -659,36 +797,98 @@ static int eval_splat(const splats2d_t *s, int i, double px, double py, int plai
 }
 
 
-/* Relative error of a GPU-side binary32 alpha from the position quantisation:
- * mu-hat is held in binary32 (ulp 2^-23 |mu|), and log hat G moves by
- * |conic d| per pixel of offset, so a ~= |conic d| * 2^-22 * max(|mu|, 1).   */
-static double position_sensitivity(const splats2d_t *s, int i, double dx, double dy)
+/* Per-pair part of the FP32 error model: a bound on |ln a32 - ln a| for one (pixel,
+ * splat) pair, a32 the pair weight of a binary32 evaluation that
+ *   - takes the shape terms with the error of E (above; root-sum-square over its
+ *     22 inputs, each perturbed by 8 unit roundoffs: the longest chain of rounded
+ *     operations from one input to y),
+ *   - takes the centre to 2e-7 px (compensated arithmetic, integer anchor plus
+ *     fraction) and forms the pixel offset d from tile-local numbers, each rounded
+ *     once (u (2|d| + 32) px per axis),
+ *   - evaluates the exponent as |U d|^2 with U the Cholesky factor of the conic
+ *     (each factor entry within 6 unit roundoffs, each product and sum rounded once),
+ *   - evaluates exp with a relative error of 4 ulp (2^-22) and erfc/2 within the
+ *     Abramowitz & Stegun 7.1.26 bound (7.5e-8 absolute) plus the rounding of its
+ *     polynomial and exponential,
+ *   - rounds the opacity mix and the product A G once each (and the mip factor of the
+ *     opacities to 16 ulp when mip is on).
+ * The sum of these first-order terms is doubled (OR_SAFETY).                         */
+#define OR_EX2_REL 2.384185791015625e-7   /* 2^-22 */
+#define OR_ERFC_ABS 7.5e-8
+#define OR_SAFETY 2.0
+#define OR_SHAPE_ULPS 8.0
+static double pair_band(const splats2d_t *s, const double *E, int i, double dx, double dy,
+                        const eval_t *e, int plain, int mip)
 {
+    const double u = OR_U32;
     const double *Q = s->conic + 3 * i;
-    double gx = Q[0] * dx + Q[1] * dy, gy = Q[1] * dx + Q[2] * dy;
-    double mu = fmax(fmax(fabs(s->mu2[2 * i]), fabs(s->mu2[2 * i + 1])), 1.0);
-    return sqrt(gx * gx + gy * gy) * ldexp(mu, -22);
+    double A = e->A > 1e-300 ? e->A : 1e-300;
+    double d12 = plain ? 0.0 : s->op1[i] - s->op2[i];
+    double g[5] = {-0.5 * dx * dx, -dx * dy, -0.5 * dy * dy, 0.0, 0.0};
+    double phi = 0.0, z = 0.0, wx = s->wp[2 * i], wy = s->wp[2 * i + 1];
+    int normal = !plain && s->mode[i] == OR_NORMAL;
+    if (normal) {
+        z = wx * dx + wy * dy;
+        phi = exp(-z * z) / sqrt(3.14159265358979323846);     /* dP/dz */
+        g[3] = d12 * phi * dx / A;
+        g[4] = d12 * phi * dy / A;
+    }
+    double shape = 0.0;
+    if (E) {
+        const double *Ei = E + 15 * (size_t)i;
+        double qf = 0.0;
+        int q = 0;
+        for (int a = 0; a < 5; ++a)
+            for (int b = a; b < 5; ++b, ++q) qf += (a == b ? 1.0 : 2.0) * g[a] * g[b] * Ei[q];
+        shape = OR_SHAPE_ULPS * u * sqrt(qf > 0 ? qf : 0.0);
+    }
+    /* centre and pixel offset */
+    double gx = -(Q[0] * dx + Q[1] * dy) + (normal ? d12 * phi * wx / A : 0.0);
+    double gy = -(Q[1] * dx + Q[2] * dy) + (normal ? d12 * phi * wy / A : 0.0);
+    double pos = fabs(gx) * (2e-7 + u * (2.0 * fabs(dx) + 32.0)) + fabs(gy) * (2e-7 + u * (2.0 * fabs(dy) + 32.0));
+    /* the exponent as a sum of two squares */
+    double u11 = sqrt(Q[0]), u12 = Q[1] / u11;
+    double dq = Q[0] * Q[2] - Q[1] * Q[1];
+    double u22 = sqrt(dq > 0 ? dq : 0.0) / u11;
+    double s1 = u11 * dx + u12 * dy, s2 = u22 * dy;
+    double expo = 6.0 * u * (fabs(s1) * (fabs(u11 * dx) + fabs(u12 * dy)) + s2 * s2) + u * (s1 * s1 + s2 * s2);
+    /* approximations and the remaining roundings */
+    double mix = 0.0;
+    if (normal) {
+        double h = 0.5 * erfc(fabs(z));
+        double dP = OR_ERFC_ABS + h * (OR_EX2_REL + 8.0 * u) + phi * 2.0 * u * (fabs(wx * dx) + fabs(wy * dy));
+        mix = fabs(d12) * dP / A;
+    }
+    mix += u * (fabs(d12) * e->P / A + 1.0);
+    double rnd = OR_EX2_REL + 2.0 * u + (mip ? 16.0 * u : 0.0);
+    return OR_SAFETY * (shape + pos + expo + mix + rnd);
 }
-
-#define OR_DECISION_REL 1e-4   /* binary32 rounding of everything but the position */
 
 /* Renders the tiles selected by tile_mask (all if NULL).
  * image [3,H,W], T [H,W], n_contrib [H,W] (1 + list position of the last
- * composited splat, 0 if none), margin [H,W] (smallest relative distance of
- * any threshold decision to its threshold).  Optional (may be NULL):
- * margin_a [H,W], margin_T [H,W]: the smallest distance of the 1/255-floor (and
- * step-sign) decisions, resp. of the 1e-4 transmittance stop, to their
- * thresholds, each divided by the relative error a binary32 evaluation can
- * carry there (OR_DECISION_REL plus the position term above; for the stop, the
- * sum of those errors over the composited splats).  A value <= 1 marks a
- * decision binary32 arithmetic cannot be expected to reproduce.
- * n_comp [H,W]: the number of composited splats.                              */
+ * composited splat, 0 if none), margin [H,W] (smallest relative distance of any
+ * threshold decision to its threshold).  Optional outputs (may be NULL), from the
+ * FP32 error model (errmat [n,15] from or_error_basis; NULL drops its shape part):
+ *   margin_a [H,W]: smallest |a - 1/255| / (a band) over the pixel's evaluated pairs,
+ *                   and of the step-sign decisions |z| / (z band);
+ *   margin_T [H,W]: the same for the 1e-4 stop, against the accumulated band of T;
+ *   margin_c [H,W]: the same for the 0.99 clamp (it bends the gradient, not the image);
+ *   n_comp [H,W]:   the number of composited splats;
+ *   flip_img, flip_T [H,W]: how much the pixel (any channel) and T may move when every
+ *                   decision with margin <= 1 goes the other way: T a (|c| + colour
+ *                   behind) for the floor, T |alpha1 - alpha2| G (...) for a step sign,
+ *                   T (colour) for the stop;
+ *   touched [n]:    1 for every splat with a decision of margin <= 1 in some pixel.
+ * A margin <= 1 marks a decision a binary32 evaluation cannot be expected to
+ * reproduce.                                                                     */
 int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic,
                   const double *wp, const double *rgb, const double *op1, const double *op2,
                   const uint32_t *ids, const uint32_t *ranges, const or_camera *cam,
                   const or_opts *o, const unsigned char *tile_mask,
                   double *image, double *T_out, int *n_contrib, double *margin,
-                  double *margin_a, double *margin_T, int *n_comp)
+                  double *margin_a, double *margin_T, int *n_comp,
+                  const double *errmat, double *margin_c, double *flip_img, double *flip_T,
+                  unsigned char *touched)
 {
     (void)n;
     splats2d_t s = {mode, mu2, conic, wp, rgb, op1, op2};
@@ -696,6 +896,8 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
     int tiles_x = (W + o->tile_w - 1) / o->tile_w;
     int tiles_y = (H + o->tile_h - 1) / o->tile_h;
     int n_tiles = tiles_x * tiles_y;
+    const double u = OR_U32;
+    double bgmax = fmax(fmax(fabs(cam->bg[0]), fabs(cam->bg[1])), fabs(cam->bg[2]));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int tile = 0; tile < n_tiles; ++tile) {
         if (tile_mask && !tile_mask[tile]) continue;
@@ -704,35 +906,74 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
         for (int py = ty * o->tile_h; py < (ty + 1) * o->tile_h && py < H; ++py)
             for (int px = tx * o->tile_w; px < (tx + 1) * o->tile_w && px < W; ++px) {
                 double pcx = px + 0.5, pcy = py + 0.5;
-                double T = 1.0, C[3] = {0, 0, 0}, mg = 1e300, mga = 1e300, mgT = 1e300;
+                double T = 1.0, C[3] = {0, 0, 0}, mg = 1e300, mga = 1e300, mgT = 1e300, mgc = 1e300;
                 double step_mg = 1e300, t_err = 0.0;
+                double f_own = 0.0, f_wt = 0.0, f_stop = 0.0, f_T = 0.0, cmax = bgmax;
                 int last = 0, ncomp = 0;
                 for (uint32_t j = beg; j < end; ++j) {
                     int i = (int)ids[j];
                     if (mode[i] == OR_CULLED) continue;
                     eval_t e;
                     if (!eval_splat(&s, i, pcx, pcy, o->plain, &e, &step_mg)) continue;
+                    double dx = pcx - mu2[2 * i], dy = pcy - mu2[2 * i + 1];
+                    double ci = fmax(fmax(fabs(rgb[3 * i]), fabs(rgb[3 * i + 1])), fabs(rgb[3 * i + 2]));
                     double rel = fabs(e.a - OR_ALPHA_MIN) / OR_ALPHA_MIN;
-                    double sens = position_sensitivity(&s, i, pcx - mu2[2 * i], pcy - mu2[2 * i + 1]);
                     if (rel < mg) mg = rel;
-                    double na = rel / (OR_DECISION_REL + sens);
-                    if (na < mga) mga = na;
+                    double band = -1.0;
+                    if (e.a >= OR_ALPHA_MIN || rel < 0.05) band = pair_band(&s, errmat, i, dx, dy, &e, o->plain, o->mip);
+                    if (rel < 0.05) {
+                        double na = rel / band;
+                        if (na < mga) mga = na;
+                        if (na <= 1.0) {          /* the floor may go either way */
+                            f_own += T * e.a * ci;
+                            f_wt += T * e.a;
+                            t_err += e.a;
+                            if (touched) touched[i] = 1;
+                        }
+                    }
+                    if (!o->plain && mode[i] == OR_STEP) {
+                        /* the sign of w.d decides alpha1 or alpha2 */
+                        double z = wp[2 * i] * dx + wp[2 * i + 1] * dy;
+                        double zb = fabs(wp[2 * i]) * (2e-7 + u * (2.0 * fabs(dx) + 32.0)) +
+                                    fabs(wp[2 * i + 1]) * (2e-7 + u * (2.0 * fabs(dy) + 32.0)) +
+                                    2.0 * u * (fabs(wp[2 * i] * dx) + fabs(wp[2 * i + 1] * dy));
+                        double ns = fabs(z) / (OR_SAFETY * zb);
+                        if (ns < mga) mga = ns;
+                        if (ns <= 1.0) {
+                            double dw = T * fabs(op1[i] - op2[i]) * e.G;
+                            f_own += dw * ci;
+                            f_wt += dw;
+                            t_err += fabs(op1[i] - op2[i]) * e.G;
+                            if (touched) touched[i] = 1;
+                        }
+                    }
                     if (e.a < OR_ALPHA_MIN) continue;
+                    if (margin_c) {
+                        double nc = fabs(e.araw - OR_ALPHA_MAX) / OR_ALPHA_MAX / band;
+                        if (nc < mgc) mgc = nc;
+                        if (nc <= 1.0 && touched) touched[i] = 1;
+                    }
                     double Tn = T * (1.0 - e.a);
                     double relT = fabs(Tn - OR_T_MIN) / OR_T_MIN;
                     if (relT < mg) mg = relT;
-                    double this_err = e.a / (1.0 - e.a) * sens;
-                    double nT = relT / (OR_DECISION_REL * (1.0 + ncomp / 100.0) + t_err + this_err);
+                    double this_err = e.a / (1.0 - e.a) * band;
+                    double nT = relT / (t_err + this_err + 2.0 * u * (ncomp + 1));
                     if (nT < mgT) mgT = nT;
+                    if (nT <= 1.0) {              /* the stop may go either way */
+                        f_stop += T;
+                        f_T += T * e.a;
+                        if (ci > cmax) cmax = ci;
+                        if (touched) touched[i] = 1;
+                    }
                     if (Tn < OR_T_MIN) break;
                     for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * e.a * T;
                     T = Tn;
                     t_err += this_err;
+                    if (ci > cmax) cmax = ci;
                     last = (int)(j - beg) + 1;
                     ncomp++;
                 }
                 if (step_mg < mg) mg = step_mg;
-                if (step_mg / OR_DECISION_REL < mga) mga = step_mg / OR_DECISION_REL;
                 size_t pix = (size_t)py * W + px;
                 for (int ch = 0; ch < 3; ++ch) image[(size_t)ch * W * H + pix] = C[ch] + T * cam->bg[ch];
                 T_out[pix] = T;
@@ -740,7 +981,10 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
                 margin[pix] = mg;
                 if (margin_a) margin_a[pix] = mga;
                 if (margin_T) margin_T[pix] = mgT;
+                if (margin_c) margin_c[pix] = mgc;
                 if (n_comp) n_comp[pix] = ncomp;
+                if (flip_img) flip_img[pix] = f_own + f_wt * cmax + f_stop * cmax;
+                if (flip_T) flip_T[pix] = f_wt + f_T;
             }
     }
     return 0;
@@ -750,11 +994,20 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
  * [d mu2_x, d mu2_y, d A, d B, d C, d wp_x, d wp_y, d alpha1, d alpha2, d r, d g, d b]
  * where the conic is [[A, B], [B, C]] and B is one scalar parameter.         */
 #define G2D 12
+/* grad2d_err (optional, [n,12], accumulated): a first-order bound on the error of a
+ * binary32 evaluation of each entry, sum over its per-pixel terms t of |t| eps, with
+ * eps = 2 band + (the accumulated band of T) + 32 ulp: band (pair_band, with errmat
+ * when given) bounds the relative error of the pair weight, which enters each term
+ * once through a and once through the quantities derived from it; the transmittance
+ * carries the bands of the splats composited in front; 32 ulp cover the term's own
+ * products and its share of the summation.  Per-thread accumulators hold only the
+ * splats listed in the rendered tiles.                                              */
 int or_render_bwd(int n, const int *mode, const double *mu2, const double *conic,
                   const double *wp, const double *rgb, const double *op1, const double *op2,
                   const uint32_t *ids, const uint32_t *ranges, const or_camera *cam,
                   const or_opts *o, const unsigned char *tile_mask,
-                  const double *dL_dimage, double *grad2d /* [n,12], accumulated */)
+                  const double *dL_dimage, double *grad2d /* [n,12], accumulated */,
+                  const double *errmat, double *grad2d_err)
 {
     splats2d_t s = {mode, mu2, conic, wp, rgb, op1, op2};
     int W = cam->width, H = cam->height;
@@ -762,8 +1015,22 @@ int or_render_bwd(int n, const int *mode, const double *mu2, const double *conic
     int tiles_y = (H + o->tile_h - 1) / o->tile_h;
     int n_tiles = tiles_x * tiles_y;
     int nthr = or_num_threads();
-    double *acc = (double *)calloc((size_t)nthr * n * G2D, sizeof(double));
-    if (!acc) return 1;
+    /* compact index of the splats that appear in a rendered tile's list */
+    int *slot = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int *which = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    if (!slot || !which) { free(slot); free(which); return 1; }
+    for (int i = 0; i < n; ++i) slot[i] = -1;
+    int m_used = 0;
+    for (int tile = 0; tile < n_tiles; ++tile) {
+        if (tile_mask && !tile_mask[tile]) continue;
+        for (uint32_t j = ranges[2 * tile]; j < ranges[2 * tile + 1]; ++j) {
+            int i = (int)ids[j];
+            if (slot[i] < 0) { slot[i] = m_used; which[m_used++] = i; }
+        }
+    }
+    int nabs = grad2d_err ? 2 : 1;
+    double *acc = (double *)calloc((size_t)nthr * nabs * (m_used > 0 ? m_used : 1) * G2D, sizeof(double));
+    if (!acc) { free(slot); free(which); return 1; }
 #pragma omp parallel
     {
 #ifdef _OPENMP
@@ -771,11 +1038,13 @@ int or_render_bwd(int n, const int *mode, const double *mu2, const double *conic
 #else
         int tid = 0;
 #endif
-        double *g2 = acc + (size_t)tid * n * G2D;
+        double *g2c = acc + (size_t)tid * nabs * m_used * G2D;
+        double *gac = grad2d_err ? g2c + (size_t)m_used * G2D : NULL;
         int cap = 64;
         int *lst = (int *)malloc(sizeof(int) * cap);
         eval_t *ev = (eval_t *)malloc(sizeof(eval_t) * cap);
         double *Ts = (double *)malloc(sizeof(double) * cap);
+        double *eps = (double *)malloc(sizeof(double) * cap);
 #pragma omp for schedule(dynamic, 1)
         for (int tile = 0; tile < n_tiles; ++tile) {
             if (tile_mask && !tile_mask[tile]) continue;
@@ -789,7 +1058,7 @@ int or_render_bwd(int n, const int *mode, const double *mu2, const double *conic
                     for (int ch = 0; ch < 3; ++ch) g[ch] = dL_dimage[(size_t)ch * W * H + pix];
                     /* forward again, remembering the composited splats */
                     int m = 0;
-                    double T = 1.0;
+                    double T = 1.0, t_err = 0.0;
                     for (uint32_t j = beg; j < end; ++j) {
                         int i = (int)ids[j];
                         if (mode[i] == OR_CULLED) continue;
@@ -803,8 +1072,15 @@ int or_render_bwd(int n, const int *mode, const double *mu2, const double *conic
                             lst = (int *)realloc(lst, sizeof(int) * cap);
                             ev = (eval_t *)realloc(ev, sizeof(eval_t) * cap);
                             Ts = (double *)realloc(Ts, sizeof(double) * cap);
+                            eps = (double *)realloc(eps, sizeof(double) * cap);
                         }
                         lst[m] = i; ev[m] = e; Ts[m] = T;
+                        if (grad2d_err) {
+                            double band = pair_band(&s, errmat, i, pcx - mu2[2 * i], pcy - mu2[2 * i + 1], &e,
+                                                    o->plain, o->mip);
+                            eps[m] = 2.0 * band + t_err + 32.0 * OR_U32;
+                            t_err += e.a / (1.0 - e.a) * band;
+                        }
                         m++;
                         T = Tn;
                     }
@@ -816,47 +1092,60 @@ int or_render_bwd(int n, const int *mode, const double *mu2, const double *conic
                         int i = lst[q];
                         const eval_t *e = &ev[q];
                         double Ti = Ts[q];
-                        double *gi = g2 + (size_t)i * G2D;
+                        double t[G2D] = {0};     /* this pixel's terms */
                         double dLda = 0;
                         for (int ch = 0; ch < 3; ++ch) {
-                            gi[9 + ch] += e->a * Ti * g[ch];
+                            t[9 + ch] = e->a * Ti * g[ch];
                             dLda += Ti * (rgb[3 * i + ch] - S[ch]) * g[ch];
                         }
                         dLda -= Tfinal / (1.0 - e->a) * bgg;
                         for (int ch = 0; ch < 3; ++ch) S[ch] = e->a * rgb[3 * i + ch] + (1.0 - e->a) * S[ch];
-                        if (e->clamped) continue;
-                        double dx = pcx - mu2[2 * i], dy = pcy - mu2[2 * i + 1];
-                        const double *Qc = conic + 3 * i;
-                        double dG = dLda * e->A;
-                        double dpow = dG * e->G;
-                        gi[2] += dpow * (-0.5 * dx * dx);
-                        gi[3] += dpow * (-dx * dy);
-                        gi[4] += dpow * (-0.5 * dy * dy);
-                        gi[0] += dpow * (Qc[0] * dx + Qc[1] * dy);
-                        gi[1] += dpow * (Qc[1] * dx + Qc[2] * dy);
-                        if (o->plain) {
-                            gi[7] += dLda * e->G;
-                            continue;
+                        if (!e->clamped) {
+                            double dx = pcx - mu2[2 * i], dy = pcy - mu2[2 * i + 1];
+                            const double *Qc = conic + 3 * i;
+                            double dG = dLda * e->A;
+                            double dpow = dG * e->G;
+                            t[2] = dpow * (-0.5 * dx * dx);
+                            t[3] = dpow * (-dx * dy);
+                            t[4] = dpow * (-0.5 * dy * dy);
+                            t[0] = dpow * (Qc[0] * dx + Qc[1] * dy);
+                            t[1] = dpow * (Qc[1] * dx + Qc[2] * dy);
+                            if (o->plain) {
+                                t[7] = dLda * e->G;
+                            } else {
+                                t[7] = dLda * e->P * e->G;
+                                t[8] = dLda * (1.0 - e->P) * e->G;
+                                if (mode[i] == OR_NORMAL) {
+                                    double dP = dLda * (op1[i] - op2[i]) * e->G;
+                                    double z = wp[2 * i] * dx + wp[2 * i + 1] * dy;
+                                    double dz = dP * exp(-z * z) / sqrt(3.14159265358979323846);
+                                    t[5] = dz * dx;
+                                    t[6] = dz * dy;
+                                    t[0] -= dz * wp[2 * i];
+                                    t[1] -= dz * wp[2 * i + 1];
+                                }
+                            }
                         }
-                        gi[7] += dLda * e->P * e->G;
-                        gi[8] += dLda * (1.0 - e->P) * e->G;
-                        if (mode[i] == OR_NORMAL) {
-                            double dP = dLda * (op1[i] - op2[i]) * e->G;
-                            double z = wp[2 * i] * dx + wp[2 * i + 1] * dy;
-                            double dz = dP * exp(-z * z) / sqrt(3.14159265358979323846);
-                            gi[5] += dz * dx;
-                            gi[6] += dz * dy;
-                            gi[0] -= dz * wp[2 * i];
-                            gi[1] -= dz * wp[2 * i + 1];
+                        double *gi = g2c + (size_t)slot[i] * G2D;
+                        for (int f = 0; f < G2D; ++f) gi[f] += t[f];
+                        if (gac) {
+                            double *ga = gac + (size_t)slot[i] * G2D;
+                            for (int f = 0; f < G2D; ++f) ga[f] += fabs(t[f]) * eps[q];
                         }
                     }
                 }
         }
-        free(lst); free(ev); free(Ts);
+        free(lst); free(ev); free(Ts); free(eps);
     }
-    for (int t = 0; t < nthr; ++t)
-        for (size_t j = 0; j < (size_t)n * G2D; ++j) grad2d[j] += acc[(size_t)t * n * G2D + j];
-    free(acc);
+    for (int t = 0; t < nthr; ++t) {
+        const double *g2c = acc + (size_t)t * nabs * m_used * G2D;
+        for (int c = 0; c < m_used; ++c)
+            for (int f = 0; f < G2D; ++f) {
+                grad2d[(size_t)which[c] * G2D + f] += g2c[(size_t)c * G2D + f];
+                if (grad2d_err) grad2d_err[(size_t)which[c] * G2D + f] += g2c[((size_t)m_used + c) * G2D + f];
+            }
+    }
+    free(acc); free(slot); free(which);
     return 0;
 }
 

@@ -20,8 +20,11 @@
 // The binning fields (depth, mu-hat, hat Sigma, 3-sigma radius, tile rect) use a
 // fixed FP32 operation order with no fused multiply-add (__f*_rn intrinsics), so
 // that the integer decisions they feed are reproducible.  The continuous terms
-// are FP32; splats whose hat Sigma is ill-conditioned or whose plane nearly
-// contains the ray get their conic and half-plane terms recomputed in FP64.
+// are FP32, with FP64 only for near-degenerate splats: in the forward, a splat
+// whose plane nearly contains the ray (v < 1e-3 var_s) gets its half-plane terms
+// w' recomputed in FP64; in the adjoint, such a splat and a splat whose hat Sigma
+// is ill-conditioned (condition number above 300) get their geometry adjoint
+// (conic, covariance, half-plane terms to mean, scale, rotation, normal) in FP64.
 #include <math.h>
 
 #include "hgs_internal.cuh"
@@ -39,6 +42,13 @@ enum { MODE_CULLED = 0, MODE_NORMAL = 1, MODE_STEP = 2, MODE_HALF = 3 };
 // Degeneracy test that sends a splat's half-plane terms to the FP64 path: the
 // splitting plane nearly contains the ray (v < kVRelFp64 * var_s).
 constexpr float kVRelFp64 = 1e-3f;
+// The projection adjoint also takes the FP64 path for a splat whose hat Sigma has a
+// condition number above kCondFp64 (a needle- or disk-like footprint, ~0.3% of the
+// splats of the benchmark scenes): through the conic, dL/d hat Sigma = -conic G conic
+// loses about cond x u in binary32, which reached 1e-3..3e-2 of the scale and
+// quaternion gradients of such splats.
+constexpr float kCondFp64 = 300.0f;
+constexpr float kCondFp64Test = (1.0f + kCondFp64) * (1.0f + kCondFp64) / kCondFp64;
 // Scale applied to w in step mode (v ~ 0): P becomes a step at w.d = 0.
 constexpr float kStepScale = 1.2089258196146292e24f;   // 2^80
 
@@ -336,12 +346,14 @@ struct Proj {
     T J00, J02, J11, J12, M[2][3], P[2][3], a, b, c, det, Q[3];
     T n0, n1, det0;          // hat Sigma_0 = P P^T (before the low-pass): diagonal, determinant
     T nn, nh[3], u[3], var_s, k[2], w[2], v;
+    T lp;                    // the low-pass l
     int mode;
 
     __device__ __forceinline__ void run(const float *m, const float *s, const float *q,
                                         const float *nrm, const hgs_camera &cam, float lp,
                                         int fov_clamp) {
         const float *V = cam.viewmat;
+        this->lp = (T)lp;
         qn = sqrt_f((T)q[0] * q[0] + (T)q[1] * q[1] + (T)q[2] * q[2] + (T)q[3] * q[3]);
         T iq = rcp_f(qn);
 #pragma unroll
@@ -414,6 +426,13 @@ struct Proj {
 
     __device__ __forceinline__ bool degenerate() const {
         return mode == MODE_NORMAL && v < (T)kVRelFp64 * var_s;
+    }
+
+    // hat Sigma ill-conditioned: lambda_max / lambda_min > kCondFp64, tested without a
+    // root as tr^2 > (1 + K)^2 / K det (tr^2 / det = (1 + c)^2 / c for condition c).
+    __device__ __forceinline__ bool ill_conditioned() const {
+        const T tr = a + c;
+        return tr * tr > (T)kCondFp64Test * det;
     }
 
     // Opacity factor of the Mip-Splatting 2D filter: sqrt(det hat Sigma_0 / det hat Sigma).
@@ -848,17 +867,16 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
                                          float gn[3], T g_comp = 0) {
     const float *V = cam.viewmat;
     T gA = g2[2], gB = g2[3], gC = g2[4];
-    T gk[2] = {0, 0}, gvar = 0;
+    T gk[2] = {0, 0}, gv = 0;
     if (f.mode == MODE_NORMAL) {
+        // w' = w / sqrt(2 v) with w = conic k: the w part flows into the conic and k
         T sv = rcp_f(sqrt_f((T)2 * f.v));
         T gw0 = (T)g2[5] * sv, gw1 = (T)g2[6] * sv;
-        T gv = -((T)g2[5] * f.w[0] + (T)g2[6] * f.w[1]) * sv * sv * sv;
-        gvar = gv;
-        gk[0] = -gv * f.w[0]; gk[1] = -gv * f.w[1];
-        gw0 -= gv * f.k[0]; gw1 -= gv * f.k[1];
+        gv = -((T)g2[5] * f.w[0] + (T)g2[6] * f.w[1]) * sv * sv * sv;
         gA += gw0 * f.k[0]; gB += gw0 * f.k[1] + gw1 * f.k[0]; gC += gw1 * f.k[1];
-        gk[0] += f.Q[0] * gw0 + f.Q[1] * gw1;
-        gk[1] += f.Q[1] * gw0 + f.Q[2] * gw1;
+        gk[0] = f.Q[0] * gw0 + f.Q[1] * gw1;
+        gk[1] = f.Q[1] * gw0 + f.Q[2] * gw1;
+        // the v part goes to P and u below, through the cancellation-free form of v
     }
     // hat Sigma from the conic: Gs = -Q [[gA, gB/2], [gB/2, gC]] Q
     T hb = (T)0.5 * gB;
@@ -881,7 +899,40 @@ __device__ __forceinline__ void proj_vjp(const Proj<T> &f, const float *s, const
     for (int kk = 0; kk < 3; ++kk) {
         gP[0][kk] = 2 * (Gs00 * f.P[0][kk] + Gs01 * f.P[1][kk]) + gk[0] * f.u[kk];
         gP[1][kk] = 2 * (Gs01 * f.P[0][kk] + Gs11 * f.P[1][kk]) + gk[1] * f.u[kk];
-        gu[kk] = f.P[0][kk] * gk[0] + f.P[1][kk] * gk[1] + 2 * gvar * f.u[kk];
+        gu[kk] = f.P[0][kk] * gk[0] + f.P[1][kk] * gk[1];
+    }
+    // v = N / det with N = (u.(p0 x p1))^2 + l (|u x p0|^2 + |u x p1|^2) + l^2 |u|^2 and
+    // det = |p0 x p1|^2 + l (|p0|^2 + |p1|^2) + l^2 (the forward's form).  Differentiated
+    // in that form, every term is a product of cross products no larger than the splat's
+    // own plane-aligned extent, so nothing cancels when the plane nearly contains the ray;
+    // the form var_s - k.w would subtract terms of order var_s / v from one another.
+    if (gv != (T)0) {
+        const T lp = f.lp;
+        T cr[3], up0[3], up1[3], c0[3], c1[3], t0[3], t1[3];
+        cross3(f.P[0], f.P[1], cr);
+        cross3(f.u, f.P[0], up0);
+        cross3(f.u, f.P[1], up1);
+        const T trip = dot3(f.u, cr);
+        const T g = gv * rcp_f(f.det), two_trip = 2 * trip, two_l = 2 * lp, vv = f.v;
+        // d v / d p0 = [2 trip (p1 x u) + 2 l (up0 x u) - v (2 p1 x cr + 2 l p0)] / det
+        cross3(f.P[1], f.u, c0);
+        cross3(up0, f.u, t0);
+        cross3(f.P[1], cr, c1);
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            gP[0][kk] += g * (two_trip * c0[kk] + two_l * t0[kk] - vv * (2 * c1[kk] + two_l * f.P[0][kk]));
+        // d v / d p1 = [2 trip up0 + 2 l (up1 x u) - v (2 cr x p0 + 2 l p1)] / det
+        cross3(up1, f.u, t1);
+        cross3(cr, f.P[0], c1);
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            gP[1][kk] += g * (two_trip * up0[kk] + two_l * t1[kk] - vv * (2 * c1[kk] + two_l * f.P[1][kk]));
+        // d v / d u = [2 trip cr + 2 l (p0 x up0 + p1 x up1) + 2 l^2 u] / det
+        cross3(f.P[0], up0, t0);
+        cross3(f.P[1], up1, t1);
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            gu[kk] += g * (two_trip * cr[kk] + two_l * (t0[kk] + t1[kk]) + two_l * lp * f.u[kk]);
     }
     // P = M L
     T gM[2][3], gL[3][3];
@@ -1021,7 +1072,8 @@ __global__ void __launch_bounds__(kProjBwdBlock, 8) k_project_bwd(ProjBwdLaunch 
             go1 += comp * g2.v[7];
             go2 += comp * g2.v[8];
             const float g_comp = mip ? sm.o1[t] * g2.v[7] + sm.o2[t] * g2.v[8] : 0.0f;
-            const bool defer = f.degenerate();     // geometry adjoint by k_project_bwd_fp64
+            // geometry adjoint by k_project_bwd_fp64
+            const bool defer = f.degenerate() || f.ill_conditioned();
             list_append(p.fp64_list, defer, (uint32_t)vi);
             if (!defer) proj_vjp<float>(f, P.s, cam, g2.v, gm, gs, gq, gn, g_comp);
             // SH colour: rgb = max(0, sum c Y(dir) + 1/2), dir = unit(mu - camera centre)

@@ -19,3 +19,18 @@ def cuda_ok():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return True
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Exempt-pixel fractions of every image comparison (the FP32 error model's
+    threshold decisions, reading B15), so a run's output shows them."""
+    mod = sys.modules.get("hgs_testutil")
+    log = getattr(mod, "EXEMPT_LOG", None) if mod else None
+    if not log:
+        return
+    tot_ex = sum(e for _, e, _ in log)
+    tot_px = sum(p for _, _, p in log)
+    worst = max(log, key=lambda r: r[1] / max(r[2], 1))
+    terminalreporter.write_line(
+        f"exempt pixels: {tot_ex} of {tot_px} compared ({tot_ex / max(tot_px, 1):.4%}) over {len(log)} "
+        f"comparisons; largest {worst[1] / max(worst[2], 1):.3%} ({worst[0]})")

@@ -4,25 +4,38 @@ import numpy as np
 
 import oracle
 
-# A pixel whose oracle decisions (1/255 floor, step-mode sign) sit within this
-# relative distance of their threshold can flip between FP32 and FP64.  The
-# oracle's margin_a / margin_T are this distance divided by the error a binary32
-# evaluation can carry (which includes the binary32 position of the splat and,
-# for the 1e-4 stop, the errors of every composited splat); <= 1 means exempt.
-EXEMPT_MARGIN = 1e-4
+# Exemptions (reading B15).  The oracle's FP32 error model bounds, per (pixel, splat)
+# pair, how far a binary32 evaluation of the pair weight can be from the FP64 value
+# (input conditioning of the shape terms, the compensated centre, the |U d|^2
+# exponent, the exp / erfc approximations; doubled).  A threshold decision within
+# that band of its threshold (1/255 floor, step sign, 1e-4 stop) may go either way:
+# the oracle marks it with a margin <= 1.  Only pixels with such a decision are
+# exempt from the 1e-4 bound, and they are still held to 1e-4 plus the largest
+# change those decisions can cause (flip_img, flip_T).
+IMAGE_ATOL = 1e-4
+# Largest fraction of exempt pixels a test accepts.  Measured: 0 to 0.05% on the
+# small scenes and config 2, 0.18-0.25% on the sampled dense tiles of configs 3-5
+# (600 to 2,200 splats per pixel list).
+MAX_EXEMPT_FRAC = 1e-3
+MAX_EXEMPT_FRAC_DENSE = 5e-3
+# Failing gradient entries: at most this fraction, each within GRAD_BAD_REL.
+GRAD_MAX_BAD_FRAC = 1e-3
+GRAD_BAD_REL = 1e-2
+
+# (test label, exempt pixels, pixels) of every comparison in this session, printed
+# in the terminal summary (tests/conftest.py)
+EXEMPT_LOG = []
 
 
 def exempt(ref):
-    """Pixels whose threshold decisions FP32 cannot be expected to reproduce."""
-    if "margin_a" not in ref:
-        return ref["margin"] <= EXEMPT_MARGIN
+    """Pixels with a floor, step-sign or stop decision FP32 cannot be expected to reproduce."""
     return (ref["margin_a"] <= 1.0) | (ref["margin_T"] <= 1.0)
 
 
-IMAGE_ATOL = 1e-4
-# One threshold flip changes a pixel by at most about a/255-scale amounts; exempt
-# pixels must still agree to this bound.
-EXEMPT_ATOL = 2e-2
+def grad_exempt(ref):
+    """exempt() plus pixels where a composited weight sits at the 0.99 clamp within the
+    FP32 band (the clamp bends the gradient, not the image)."""
+    return exempt(ref) | (ref["margin_c"] <= 1.0)
 
 
 def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persistent=True,
@@ -60,22 +73,30 @@ def gpu_render(sc, cams, tile=(16, 16), batch=0, lowpass=0.3, plain=False, persi
     return out
 
 
-def compare_image(gpu_img, gpu_T, gpu_nc, ref, atol=IMAGE_ATOL, max_exempt_frac=5e-2):
-    """Max-abs image/T error on pixels away from threshold decisions; n_contrib equal there.
-    Pixels with a decision within EXEMPT_MARGIN of its threshold (long lists make
-    hundreds of decisions per pixel) are held to EXEMPT_ATOL only."""
-    ok = ~exempt(ref)
-    n_ex = int((~ok).sum())
-    assert n_ex <= max(4, max_exempt_frac * ok.size), f"{n_ex} exempt pixels of {ok.size}"
+def compare_image(gpu_img, gpu_T, gpu_nc, ref, pix=None, max_exempt_frac=MAX_EXEMPT_FRAC, label=""):
+    """Image and final T within IMAGE_ATOL on every non-exempt pixel, n_contrib equal there;
+    exempt pixels within IMAGE_ATOL + the oracle's flip bound; at most max_exempt_frac of
+    the pixels exempt.  pix (bool [H,W], optional) selects the pixels compared (the GPU
+    arrays are then [3,K], [K], [K] over the selected pixels in row-major order)."""
+    ex = exempt(ref)
+    rimg, rT, rnc, fi, fT = ref["image"], ref["T"], ref["n_contrib"], ref["flip_img"], ref["flip_T"]
+    if pix is not None:
+        ex, rimg, rT, rnc, fi, fT = ex[pix], rimg[:, pix], rT[pix], rnc[pix], fi[pix], fT[pix]
+    ok = ~ex
+    n_ex, n_px = int(ex.sum()), int(ex.size)
+    frac = n_ex / max(n_px, 1)
+    EXEMPT_LOG.append((label, n_ex, n_px))
+    tag = f"{label}: {n_ex} of {n_px} pixels exempt ({frac:.3%})"
+    assert frac <= max_exempt_frac, tag + f", above the cap {max_exempt_frac:.2%}"
+    err = np.abs(gpu_img.astype(np.float64) - rimg).max(0)
+    terr = np.abs(gpu_T.astype(np.float64) - rT)
     if n_ex:
-        ex_err = np.abs(gpu_img.astype(np.float64) - ref["image"])[:, ~ok]
-        assert ex_err.max() <= EXEMPT_ATOL, f"exempt pixel error {ex_err.max():.3g}"
-    err = np.abs(gpu_img.astype(np.float64) - ref["image"])[:, ok]
-    terr = np.abs(gpu_T.astype(np.float64) - ref["T"])[ok]
-    assert err.size == 0 or err.max() <= atol, f"image max abs err {err.max():.3g}"
-    assert terr.size == 0 or terr.max() <= atol, f"T max abs err {terr.max():.3g}"
-    assert np.array_equal(gpu_nc[ok], ref["n_contrib"][ok])
-    return dict(max_err=float(err.max()) if err.size else 0.0, exempt=n_ex)
+        over = (err[ex] > IMAGE_ATOL + fi[ex]).sum() + (terr[ex] > IMAGE_ATOL + fT[ex]).sum()
+        assert over == 0, tag + f"; {over} exempt pixel values beyond 1e-4 + their flip bound"
+    assert not ok.any() or err[ok].max() <= IMAGE_ATOL, tag + f"; image max abs err {err[ok].max():.3g}"
+    assert not ok.any() or terr[ok].max() <= IMAGE_ATOL, tag + f"; T max abs err {terr[ok].max():.3g}"
+    assert np.array_equal(np.asarray(gpu_nc)[ok], rnc[ok]), tag + "; n_contrib differs"
+    return dict(max_err=float(err[ok].max()) if ok.any() else 0.0, exempt=n_ex, frac=frac)
 
 
 def grad_close(g, ref, rel=1e-3, floor_frac=1e-3):
@@ -87,11 +108,43 @@ def grad_close(g, ref, rel=1e-3, floor_frac=1e-3):
     return bad, scale
 
 
+def check_grads(got, ref, touched_rows=None, label="", err=None, max_bad_frac=GRAD_MAX_BAD_FRAC):
+    """Gradient parity: every entry within 1e-3 relative (floor 1e-3 of the tensor's
+    largest entry) of the FP64 adjoint, except at most max_bad_frac of the entries.
+    Each of those must be accounted for by the FP32 error model: its splat has a
+    marked threshold decision in some pixel (touched_rows, bool per leading index), or
+    the model's first-order error bound for the entry (err, the oracle's err_* arrays)
+    itself exceeds the 1e-3 bar (an entry binary32 arithmetic cannot be expected to get
+    to 1e-3).  And each must be within GRAD_BAD_REL, or within its error bound where
+    that is larger."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    bad, scale = grad_close(got, ref)
+    nb = int(bad.sum())
+    tag = f"{label}: {nb} of {bad.size} entries beyond 1e-3"
+    assert nb <= max(max_bad_frac * bad.size, 0), tag
+    if nb:
+        dev = np.abs(got - ref)[bad]
+        cap = GRAD_BAD_REL * scale[bad]
+        if err is not None:
+            cap = np.maximum(cap, np.asarray(err, np.float64)[bad])
+        worst = (dev / scale[bad]).max()
+        assert np.all(dev <= cap), tag + f"; worst {worst:.3g} relative, beyond 1e-2 and its error bound"
+        explained = np.zeros(nb, bool)
+        if touched_rows is not None:
+            explained |= np.asarray(touched_rows, bool)[np.nonzero(bad)[0]]
+        if err is not None:
+            explained |= (np.asarray(err, np.float64) > 1e-3 * scale)[bad]
+        assert explained.all(), tag + f"; {int((~explained).sum())} not accounted for by the FP32 error model"
+    return nb
+
+
 def masked_upstream(dL_list, refs):
-    """dL/dimage with exempt pixels zeroed (both sides get the same array)."""
+    """dL/dimage with the gradient-exempt pixels (grad_exempt) zeroed; both sides get
+    the same array."""
     out = []
     for d, r in zip(dL_list, refs):
         d = np.array(d, np.float32, copy=True)
-        d[:, exempt(r)] = 0.0
+        d[:, grad_exempt(r)] = 0.0
         out.append(d)
     return out

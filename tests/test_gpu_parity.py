@@ -1,16 +1,19 @@
 """CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
 Bars: sort order, tile ranges, depth keys and tile rects bit-exact; images and
-final transmittance within 1e-4 max-abs on pixels whose decisions are not
-within 1e-4 (relative) of a threshold; n_contrib equal there; gradients within
-1e-3 relative (floor 1e-3 of the tensor's largest entry) of the FP64 adjoint,
-with the upstream gradient zeroed on the exempt pixels.
+final transmittance within 1e-4 max-abs on every pixel none of whose threshold
+decisions lies within the oracle's FP32 error band (reading B15), n_contrib
+equal there, the others within 1e-4 plus the change their decisions can cause,
+and at most 0.1% of pixels exempt; gradients within 1e-3 relative (floor 1e-3
+of the tensor's largest entry) of the FP64 adjoint, with the upstream gradient
+zeroed on the exempt pixels, except at most 0.1% of entries, each within 1e-2
+and on a splat with a marked decision.
 """
 import numpy as np
 import pytest
 
 import oracle
-from hgs_testutil import compare_image, exempt, gpu_render, grad_close, masked_upstream
+from hgs_testutil import check_grads, compare_image, exempt, gpu_render, masked_upstream
 from paper_2406_02720_b300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +42,7 @@ def test_projection_fields(cuda_ok, cfg1):
     # centre = integer anchor + remainder, to ~1e-7 px of the FP64 centre
     assert np.all(rec[vis, 0:2] == np.round(rec[vis, 0:2]))
     mu = rec[vis, 0:2] + rec[vis, 2:4]
-    assert np.abs(mu - pr["mu2"][vis]).max() < 2e-6
+    assert np.abs(mu - pr["mu2"][vis]).max() < 2e-7        # the FP32 error model's centre bound
     assert np.abs(mu - pr["canon_mu"][vis]).max() < 1e-3      # and close to the binning centre
     u11, u12, u22 = rec[vis, 4], rec[vis, 5], rec[vis, 6]
     Q = np.stack([u11 * u11, u11 * u12, u12 * u12 + u22 * u22], 1)     # conic = U^T U
@@ -71,7 +74,7 @@ def test_forward_image_ragged(cuda_ok, tile, batch):
     sc, cams = _ragged_scene()
     out = gpu_render(sc, cams, tile=tile, batch=batch)
     ref = oracle.render(sc, cams[0], tile=tile)
-    info = compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label=f"ragged {tile} b{batch}")
     assert ref["n_contrib"].max() > 5
 
 
@@ -79,7 +82,7 @@ def test_forward_config1(cuda_ok, cfg1):
     sc, cams = cfg1
     out = gpu_render(sc, cams)
     ref = oracle.render(sc, cams[0])
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="config1")
     assert (ref["T"] < 0.01).mean() > 0.01      # early termination happens in this scene
 
 
@@ -108,12 +111,11 @@ def test_plain_mode_against_oracle(cuda_ok):
     assert np.abs(half["image"] - ref["image"]).max() > 1e-2
     dL = masked_upstream(scenes.upstream_grad(103, cams), [ref])
     out = gpu_render(sc, cams, plain=True, dL=dL)
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="plain mode")
     gref = oracle.render_bwd(sc, cams[0], dL[0], plain=True, proj=ref["proj"], bins=ref["bins"])
     assert np.all(out["grads"]["opac2"] == 0.0) and np.all(out["grads"]["normals"] == 0.0)
     for k in ("means", "scales", "quats", "opac1", "sh"):
-        bad, _ = grad_close(out["grads"][k], gref[k])
-        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
+        check_grads(out["grads"][k], gref[k], ref["touched"], label=f"plain mode {k}", err=gref["err_" + k])
 
 
 def test_complement_symmetry(cuda_ok):
@@ -133,18 +135,14 @@ def test_gradients_against_fp64_adjoint(cuda_ok):
     ref = oracle.render(sc, cams[0])
     dL = masked_upstream(scenes.upstream_grad(102, cams), [ref])
     out = gpu_render(sc, cams, dL=dL)
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="gradient scene")
     gref = oracle.render_bwd(sc, cams[0], dL[0], proj=ref["proj"], bins=ref["bins"])
     # screen-space gradients first (compositing adjoint), then parameters
     g2 = out["grad2d"][0]
     vis = ref["proj"]["mode"] == oracle.NORMAL
-    bad, _ = grad_close(g2[vis], gref["grad2d"][vis])
-    assert bad.mean() < 2e-3, f"grad2d: {bad.sum()} of {bad.size}"
-    report = {}
+    check_grads(g2[vis], gref["grad2d"][vis], ref["touched"][vis], label="grad2d", err=gref["grad2d_err"][vis])
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
-        bad, _ = grad_close(out["grads"][k], gref[k])
-        report[k] = (int(bad.sum()), bad.size)
-        assert bad.mean() < 2e-3, (k, report[k])
+        check_grads(out["grads"][k], gref[k], ref["touched"], label=k, err=gref["err_" + k])
 
 
 @pytest.mark.parametrize("tile,batch,persistent", [((8, 8), 32, True), ((32, 8), 128, False),
@@ -158,14 +156,13 @@ def test_gradients_other_tiles_and_batches(cuda_ok, tile, batch, persistent):
     ref = oracle.render(sc, cams[0], tile=tile)
     dL = masked_upstream(scenes.upstream_grad(104, cams), [ref])
     out = gpu_render(sc, cams, tile=tile, batch=batch, persistent=persistent, dL=dL)
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label=f"gradients {tile} b{batch}")
     gref = oracle.render_bwd(sc, cams[0], dL[0], tile=tile, proj=ref["proj"], bins=ref["bins"])
     vis = ref["proj"]["mode"] == oracle.NORMAL
-    bad, _ = grad_close(out["grad2d"][0][vis], gref["grad2d"][vis])
-    assert bad.mean() < 2e-3, f"grad2d: {bad.sum()} of {bad.size}"
+    check_grads(out["grad2d"][0][vis], gref["grad2d"][vis], ref["touched"][vis], label=f"grad2d {tile}",
+                err=gref["grad2d_err"][vis])
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
-        bad, _ = grad_close(out["grads"][k], gref[k])
-        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
+        check_grads(out["grads"][k], gref[k], ref["touched"], label=f"{k} {tile} b{batch}", err=gref["err_" + k])
 
 
 def test_multiview_persistent_matches_per_tile_launch(cuda_ok):
@@ -184,7 +181,7 @@ def test_multiview_persistent_matches_per_tile_launch(cuda_ok):
     # each view against its own oracle run
     for v, cam in enumerate(cams):
         ref = oracle.render(sc, cam)
-        compare_image(b["images"][v], b["T"][v], b["n_contrib"][v], ref)
+        compare_image(b["images"][v], b["T"][v], b["n_contrib"][v], ref, label=f"multi-view {v}")
     # global sort: the keys of view v are the oracle keys shifted by the view's tile offset
     off = 0
     for v, cam in enumerate(cams):
@@ -209,9 +206,9 @@ def test_multiview_gradients_sum_over_views(cuda_ok):
     for c, d, r in zip(cams, dL, refs):
         g = oracle.render_bwd(sc, c, d, proj=r["proj"], bins=r["bins"])
         tot = g if tot is None else {k: tot[k] + g[k] for k in tot}
+    touched = np.logical_or.reduce([r["touched"] for r in refs])
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
-        bad, _ = grad_close(out["grads"][k], tot[k])
-        assert bad.mean() < 2e-3, k
+        check_grads(out["grads"][k], tot[k], touched, label=f"two views {k}", err=tot["err_" + k])
 
 
 def test_capacity_overflow_sets_status_and_count(cuda_ok):
@@ -246,4 +243,4 @@ def test_empty_and_all_culled(cuda_ok):
     one = sc.subset(np.arange(1))
     out = gpu_render(one, cams)
     ref = oracle.render(one, cams[0])
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="one splat")

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from hgs_testutil import compare_image, gpu_render, grad_close, masked_upstream
+from hgs_testutil import check_grads, compare_image, gpu_render, masked_upstream
 from paper_2406_02720_b300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -41,11 +41,10 @@ def test_grazing_disks_against_oracle(cuda_ok):
     assert np.all(np.abs(wp - wr).max(1) <= 1e-5 * np.abs(wr).max(1)), np.abs(wp - wr).max()
     assert np.array_equal(out["keys"], ref["bins"]["keys"])
     assert np.array_equal(out["ids"], ref["bins"]["ids"])
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="grazing disks 100k")
     gref = oracle.render_bwd(sc, cam, dL[0], proj=pr, bins=ref["bins"])
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
-        bad, _ = grad_close(out["grads"][k], gref[k])
-        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
+        check_grads(out["grads"][k], gref[k], ref["touched"], label=f"grazing disks {k}", err=gref["err_" + k])
 
 
 def test_equal_opacity_copy_is_plain_3dgs(cuda_ok):
@@ -67,8 +66,7 @@ def test_grazing_disks_with_mip(cuda_ok):
     dL = masked_upstream(scenes.upstream_grad(106, cams), [ref])
     out = gpu_render(sc, cams, dL=dL, mip=True)
     assert len(out["fp64_fwd"]) >= 10                   # the FP64 path is exercised
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="grazing disks mip")
     gref = oracle.render_bwd(sc, cam, dL[0], proj=pr, bins=ref["bins"], mip=True)
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
-        bad, _ = grad_close(out["grads"][k], gref[k])
-        assert bad.mean() < 2e-3, (k, int(bad.sum()), bad.size)
+        check_grads(out["grads"][k], gref[k], ref["touched"], label=f"grazing disks mip {k}", err=gref["err_" + k])
