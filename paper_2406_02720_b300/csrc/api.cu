@@ -4,22 +4,26 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "hgs_internal.cuh"
 
 namespace hgs {
 
+// SM count of the current device, looked up once per device (atomic: threads making
+// their first calls at the same time store the same value).
 int num_sms() {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
-    int slot = dev & 63;
-    if (!cache[slot]) {
-        int v = 0;
+    std::atomic<int> &slot = cache[dev & 63];
+    int v = slot.load(std::memory_order_relaxed);
+    if (!v) {
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cache[slot] = v > 0 ? v : 1;
+        v = v > 0 ? v : 1;
+        slot.store(v, std::memory_order_relaxed);
     }
-    return cache[slot];
+    return v;
 }
 
 }  // namespace hgs

@@ -5,21 +5,23 @@
 // Who cannot allocate: a plug-in running inside a host application that owns
 // the whole device-memory budget and forbids its plug-ins to call the CUDA
 // allocator; a real-time loop that cannot afford a driver allocation, which may
-// synchronise the device; code that enqueues work while a stream is being
-// captured, where allocation calls are not allowed.  Such callers still provide
-// the inputs and the outputs (keys, ids, ranges, pair count, status); only the
-// scratch moves into the library.
+// synchronise the device.  Such callers still provide the inputs and the
+// outputs (keys, ids, ranges, pair count, status); only the scratch moves into
+// the library.
 //
 // The array is kHgsStaticScratchBytes (HGS_BIN_STATIC_SCRATCH_BYTES) bytes.  Every
 // GPU that loads this code holds it until the process exits.  Its device address
-// is looked up once per device, on the first call made with that device current,
-// with cudaGetSymbolAddress; that first call should therefore come before any
-// stream capture.  All calls share the one array and it keeps the previous
-// call's contents: the binning kernels clear everything that must start at zero
-// (the control block with the digit totals) at the start of each
-// call, and overwrite the rest before reading it.  Calls whose work overlaps on
-// the GPU (other streams, other threads) race on the array; calls in order on
-// one stream do not.
+// is looked up with cudaGetSymbolAddress on the first call made with a device
+// current, and again whenever that device's context has changed since (after a
+// cudaDeviceReset the old address is dead); that first call should therefore
+// come before any stream capture.  All calls share the one array and it keeps the
+// previous call's contents: the binning kernels clear everything that must start
+// at zero (the control block with the digit totals) at the start of each call,
+// and overwrite the rest before reading it.  Calls whose work overlaps on the GPU
+// (other streams, other threads) race on the array; calls in order on one stream
+// do not.
+#include <cuda.h>   // driver types only (CUcontext, CUresult); no link against libcuda
+
 #include <mutex>
 
 #include "hgs_internal.cuh"
@@ -32,22 +34,59 @@ static __device__ __align__(256) unsigned char g_bin_scratch[kHgsStaticScratchBy
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+struct Cached {
+    unsigned long long ctx_id;   // driver context the address belongs to (0: none yet)
+    void *ptr;
+};
+Cached g_scratch[kMaxDevices] = {};
 
-// Device address of g_bin_scratch for the current device (looked up once).
+// The unique id of the calling thread's current driver context (0 if there is none
+// or the driver does not provide the query).  The two driver entry points are
+// resolved at run time through the runtime, so the library needs no link against
+// the driver library and still loads on a machine without a GPU.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_bin_scratch for the current device, looked up on the first
+// call and again when the device's context is no longer the one of the cached
+// address.
 cudaError_t scratch_for_current_device(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    Cached &c = g_scratch[dev];
+    const unsigned long long id = current_context_id();
+    if (!c.ptr || id == 0 || id != c.ctx_id) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_bin_scratch);
+        e = cudaGetSymbolAddress(&p, g_bin_scratch);   // also makes the primary context current
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
+        c.ptr = p;
+        c.ctx_id = current_context_id();
     }
-    *out = g_scratch_ptr[dev];
+    *out = c.ptr;
     return cudaSuccess;
 }
 

@@ -22,6 +22,8 @@
 // consecutive addresses.
 #include <algorithm>
 
+#include <mutex>
+
 #include "hgs_internal.cuh"
 
 namespace hgs {
@@ -578,24 +580,35 @@ __global__ void __launch_bounds__(kBlock) k_ranges(const uint32_t *__restrict__ 
     }
 }
 
-// Resident blocks per SM of the downsweep and of the upsweep/ranges kernels (the same
-// on every device of this architecture); grids are these times the current device's
-// SM count.
-int g_occ_sweep = 0, g_occ_aux = 0;
+// Resident blocks per SM of the downsweep and of the upsweep/ranges kernels; grids are
+// these times the current device's SM count.  Set up once per device (std::call_once,
+// so threads making their first calls at the same time do not race): the downsweep's
+// shared-memory limit is a per-device attribute and has to be raised in each device's
+// context.
+struct LaunchShapes {
+    std::once_flag once;
+    int sweep = 1, aux = 1;
+};
+LaunchShapes g_shapes[64];
 
-void init_launch_shapes() {
-    if (g_occ_sweep) return;
-    int occ = 0, occ2 = 0;
-    cudaFuncSetAttribute(k_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
-    cudaFuncSetAttribute(k_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_downsweep<false>, kBlock, sizeof(DownSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_upsweep, kBlock, 0);
-    g_occ_aux = std::max(occ2, 1);
-    g_occ_sweep = std::max(occ, 1);
+const LaunchShapes &launch_shapes() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    LaunchShapes &ls = g_shapes[dev & 63];
+    std::call_once(ls.once, [&ls] {
+        int occ = 0, occ2 = 0;
+        cudaFuncSetAttribute(k_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
+        cudaFuncSetAttribute(k_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_downsweep<false>, kBlock, sizeof(DownSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_upsweep, kBlock, 0);
+        ls.aux = std::max(occ2, 1);
+        ls.sweep = std::max(occ, 1);
+    });
+    return ls;
 }
 
-int sweep_blocks() { return num_sms() * g_occ_sweep; }
-int aux_blocks() { return num_sms() * g_occ_aux; }
+int sweep_blocks() { return num_sms() * launch_shapes().sweep; }
+int aux_blocks() { return num_sms() * launch_shapes().aux; }
 
 // One radix pass over cnt elements: upsweep, digit scan, downsweep.
 cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout, uint64_t *kout64,
@@ -643,7 +656,7 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
     int tile_bits = 1;
     while ((1ll << tile_bits) < (long long)total_tiles) ++tile_bits;
     const int tile_passes = (tile_bits + kRadixBits - 1) / kRadixBits;
-    init_launch_shapes();
+    launch_shapes();
     if ((e = cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.num_pairs, 0, sizeof(uint64_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, s)) != cudaSuccess) return e;

@@ -38,6 +38,7 @@
 // Persistent mode (the default): a grid of resident blocks pops tiles from an
 // atomic queue whose order is heaviest-first (bucketed by list length).
 #include <algorithm>
+#include <atomic>
 
 #include "hgs_internal.cuh"
 
@@ -648,13 +649,15 @@ cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
         kern<<<items, NT, 0, s>>>(p);
         return cudaGetLastError();
     }
-    // resident blocks per SM (the same on every device of this architecture), times the
-    // current device's SM count
-    static int occ = 0;
+    // resident blocks per SM (assumed the same on every device of this architecture: the
+    // kernels use only static shared memory), times the current device's SM count; atomic,
+    // since threads making their first calls at the same time store the same value
+    static std::atomic<int> occ_cache{0};
+    int occ = occ_cache.load(std::memory_order_relaxed);
     if (!occ) {
-        int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, 0);
-        occ = std::max(o, 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+        occ = std::max(occ, 1);
+        occ_cache.store(occ, std::memory_order_relaxed);
     }
     kern<<<std::min(num_sms() * occ, items), NT, 0, s>>>(p);
     return cudaGetLastError();
