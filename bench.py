@@ -229,7 +229,8 @@ def run_gpu(args):
 
     # ---- work counters for the roofline (one extra forward, not timed) ------------------
     stats = rast.stats(dL)
-    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks)
+    alu = measure_alu_peaks(dev)
+    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks, alu)
 
     # ---- end to end through host buffers --------------------------------------------------
     e2e = run_e2e(args, rast, g, dL, grads, pixels, dev)
@@ -249,7 +250,8 @@ def run_gpu(args):
                    "pairs": n_pairs, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
         "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
-        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles),
+        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles, alu),
+        "alu_peaks": alu,
         "clocks": clocks,
         "e2e": e2e, "e2e_params_over_pcie": e2e_full, "gpu_launches": launches * args.steps,
     }
@@ -321,10 +323,10 @@ def alg_bytes(n, n_pairs, total_tiles):
 #   comp   : transmittance update and stop test (3), colour accumulation (4)  7 FP32
 #   contrib: backward adjoint of one composited pair (T rebuilt by division,
 #            colour-behind recurrence as one dot product, 12 gradients)     39 FP32 + 1 MUFU
-#   red    : fold of 12 gradients over lane pairs (one shuffle+add
-#            level, all 32 lanes) when more than 12 lanes contribute    384 FP32
+# The backward's fold of lane pairs before its atomics (counted as bwd_warp_red) is
+# the kernel's own reduction overhead, not the method's arithmetic, and is not counted.
 OPS = {"fwd": {"fp32": {"fwd_visit": 8, "fwd_full": 16, "fwd_comp": 7}, "mufu": {"fwd_full": 3}},
-       "bwd": {"fp32": {"bwd_visit": 8, "bwd_full": 16, "bwd_contrib": 39, "bwd_warp_red": 384},
+       "bwd": {"fp32": {"bwd_visit": 8, "bwd_full": 16, "bwd_contrib": 39},
                "mufu": {"bwd_full": 3, "bwd_contrib": 1}}}
 
 
@@ -360,7 +362,53 @@ def profiled_traffic(phase):
     return float(vals["traffic_bytes_per_launch"])
 
 
-def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
+def measure_alu_peaks(dev, repeats=5):
+    """FP32 FMA and MUFU ex2 lane-operation rates of this GPU, measured with the
+    library's issue-rate probe (independent chains, 2 blocks of 512 threads per SM),
+    timed with CUDA events on the launching stream; the best of `repeats` launches of
+    about 10 ms each, with the SM clock sampled meanwhile."""
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes_void_p(stream.cuda_stream)
+    out = {}
+    clk = ClockSampler(dev.index or 0)
+    for kind, name, iters in ((0, "fp32_fma", 20000), (1, "mufu_ex2", 2500)):
+        H.hgs_probe_peak(kind, 2, 64, ctypes_void_p(sink.data_ptr()), sp)     # warm-up
+        best = 0.0
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = H.hgs_probe_peak(kind, 2, iters, ctypes_void_p(sink.data_ptr()), sp)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, ops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name] = best
+    torch.cuda.synchronize()
+    out["clocks"] = clk.stop()
+    out["unit"] = "T lane-op/s"
+    out["method"] = ("hgs_probe_peak: independent FMA / ex2.approx chains, 2 x 512 threads per SM, "
+                     f"best of {repeats} ~10 ms launches, CUDA events")
+    return out
+
+
+def ctypes_void_p(x):
+    import ctypes
+    return ctypes.c_void_p(x)
+
+
+def alu_peaks(measured):
+    """(FP32, MUFU) lane-op peaks in T/s and their source: the probe's measurement
+    when there is one, else 148 SMs x (128 | 16) lanes x the maximum SM clock."""
+    if measured and measured.get("fp32_fma") and measured.get("mufu_ex2"):
+        return measured["fp32_fma"], measured["mufu_ex2"], "measured (hgs_probe_peak)"
+    mhz = _peaks().get("sm_max_mhz", 2032.0)
+    return (148 * 128 * mhz * 1e6 / 1e12, 148 * 16 * mhz * 1e6 / 1e12,
+            f"computed: 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz")
+
+
+def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     src = "of measured" if hbm else "of fallback"
@@ -368,10 +416,7 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
     dom = max(phases, key=phases.get)
     out = {"dominant": dom, "phase_ms": phases[dom]}
     if dom in ("render_fwd", "render_bwd") and stats:
-        sms = 148
-        mhz = peaks.get("sm_max_mhz", 2032.0)
-        fp32_peak = sms * 128 * mhz * 1e6 / 1e12          # T FP32 lane-ops / s
-        mufu_peak = sms * 16 * mhz * 1e6 / 1e12           # T MUFU lane-ops / s
+        fp32_peak, mufu_peak, peak_src = alu_peaks(measured)
         key = "fwd" if dom == "render_fwd" else "bwd"
         fp32, mufu = alu_work(stats, key)
         t = phases[dom] * 1e-3
@@ -384,8 +429,7 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
             out.update({"bound": "alu", "achieved": mufu / t / 1e12, "peak": mufu_peak, "unit": "T MUFU-op/s",
                         "frac": f_mufu})
         out.update({"traffic": profiled_traffic(dom), "frac_fp32": f_fp32, "frac_mufu": f_mufu,
-                    "note": f"peak from 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz; algorithmic ops "
-                            "= counted events x ops per event"})
+                    "note": f"peak {peak_src}; algorithmic ops = counted events x ops per event"})
     else:
         b = alg_bytes(n, n_pairs, total_tiles).get(dom, 0)
         ach = b / (phases[dom] * 1e-3) / 1e9
@@ -394,7 +438,7 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks):
     return out
 
 
-def phase_rooflines(phases, stats, n_pairs, n, total_tiles):
+def phase_rooflines(phases, stats, n_pairs, n, total_tiles, measured=None):
     """HBM fraction of the memory-bound phases and ALU fractions of the compositing
     phases (each against its own bound; algorithmic bytes/ops per launch)."""
     peaks = _peaks()
@@ -402,12 +446,12 @@ def phase_rooflines(phases, stats, n_pairs, n, total_tiles):
     out = {}
     for k, b in alg_bytes(n, n_pairs, total_tiles).items():
         out[k] = {"bound": "hbm", "GBs": b / (phases[k] * 1e-3) / 1e9, "frac": b / (phases[k] * 1e-3) / 1e9 / hbm}
-    mhz = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak, mufu_peak, _ = alu_peaks(measured)
     for key, ph in (("fwd", "render_fwd"), ("bwd", "render_bwd")):
         fp32, mufu = alu_work(stats, key)
         t = phases[ph] * 1e-3
-        out[ph] = {"bound": "alu", "frac_fp32": fp32 / t / (148 * 128 * mhz * 1e6),
-                   "frac_mufu": mufu / t / (148 * 16 * mhz * 1e6)}
+        out[ph] = {"bound": "alu", "frac_fp32": fp32 / t / (fp32_peak * 1e12),
+                   "frac_mufu": mufu / t / (mufu_peak * 1e12)}
     return out
 
 

@@ -222,17 +222,19 @@ hgs_status hgs_bin(const hgs_proj *proj, int n, const hgs_camera *cams_host, int
  * library instead of caller memory; the paper has no counterpart (it is an
  * interface for callers, not part of the method).  It is for callers that must
  * not allocate device memory: plug-ins inside a host application that owns the
- * device-memory budget, real-time loops that cannot afford a driver allocation
- * (which may synchronise the device), and code enqueueing work while a stream is
- * being captured, where allocation is not allowed.  The caller still provides
+ * device-memory budget, and real-time loops that cannot afford a driver
+ * allocation (which may synchronise the device).  The caller still provides
  * every input and output; this call allocates nothing.
  * Limit: hgs_bin_workspace_size(n, n_views, pair_capacity) must not exceed
  * HGS_BIN_STATIC_SCRATCH_BYTES (32 MiB, held on every GPU that loads the library
  * until the process exits), else HGS_ERR_CAPACITY and nothing is enqueued.
  * The first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (different streams or threads)
- * race; calls in order on one stream are safe.  Errors otherwise as hgs_bin. */
+ * device address, and a call looks it up again when the device's context has
+ * changed since (e.g. after cudaDeviceReset); make that first call before any
+ * stream capture.  All calls share the array, which keeps the previous call's
+ * contents (the call clears what must start at zero): calls that overlap on the
+ * GPU (different streams or threads) race; calls in order on one stream are
+ * safe.  Errors otherwise as hgs_bin. */
 #define HGS_BIN_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 hgs_status hgs_bin_static(const hgs_proj *proj, int n, const hgs_camera *cams_host, int n_views,
                           const hgs_config *cfg, size_t pair_capacity, uint64_t *keys_out,
@@ -307,6 +309,19 @@ hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, co
                             const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
                             uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
                             unsigned long long *counters, int *dev_status, void *stream);
+
+/* Issue-rate probe for the compositing kernels' roofline (the paper has no
+ * counterpart: it measures this GPU, not the method).  kind 0 runs independent
+ * chains of FP32 fused multiply-adds, kind 1 independent chains of the MUFU
+ * ex2.approx instruction, on blocks_per_sm (1-4) blocks of 512 threads per SM,
+ * each thread doing iters x 16 x 8 operations.  *lane_ops (host, optional)
+ * receives the number of lane-operations enqueued, so that a caller timing the
+ * launch with events on `stream` gets lane-operations per second.  sink is a
+ * device float the kernel may write (never in practice); it exists only so
+ * that the arithmetic is not optimised away.  HGS_ERR_INVALID on a bad
+ * argument (nothing enqueued). */
+hgs_status hgs_probe_peak(int kind, int blocks_per_sm, int iters, float *sink, double *lane_ops,
+                          void *stream);
 
 /* ---- misc ------------------------------------------------------------------- */
 const char *hgs_status_string(hgs_status s);

@@ -101,6 +101,8 @@ def lib():
         L.hgs_render_bwd.restype = c_int
         L.hgs_render_bwd.argtypes = [POINTER(HgsGaussians), POINTER(HgsProj), vp, vp, _CAM_P, vp, c_int,
                                      _CFG_P, vp, c_size_t, vp, vp, vp, vp, POINTER(HgsGaussianGrads), vp, vp]
+        L.hgs_probe_peak.restype = c_int
+        L.hgs_probe_peak.argtypes = [c_int, c_int, c_int, vp, POINTER(ctypes.c_double), vp]
         _LIB = L
     return _LIB
 
@@ -196,6 +198,14 @@ def hgs_render_stats(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws
     _check(lib().hgs_render_stats(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
                                   ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, dL_dimage, grad2d,
                                   counters, dev_status, stream), "hgs_render_stats")
+
+
+def hgs_probe_peak(kind, blocks_per_sm, iters, sink, stream) -> float:
+    """Enqueues the FMA (kind 0) or ex2 (kind 1) issue-rate probe; returns the
+    lane-operations it performs."""
+    ops = ctypes.c_double(0.0)
+    _check(lib().hgs_probe_peak(kind, blocks_per_sm, iters, sink, ctypes.byref(ops), stream), "hgs_probe_peak")
+    return ops.value
 
 
 STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd_contrib", "bwd_warp_red"]
