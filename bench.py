@@ -247,7 +247,10 @@ def run_gpu(args):
                    "tile": f"{args.tile_w}x{args.tile_h}",
                    "compositing": "persistent heaviest-first queue" if args.persistent else "one block per tile",
                    "batch": args.batch or f"{args.tile_w * args.tile_h} fwd / {min(2 * args.tile_w * args.tile_h, 512)} bwd",
-                   "pairs": n_pairs, "parallelism": f"replicas x{ws}",
+                   "pairs": n_pairs,
+                   "parallelism": (f"replicas x{ws}" if ws == 1 else
+                                   f"replicas x{ws}; view-sharded multi-view step with one gradient "
+                                   "all-reduce in 'sharded'"),
                    "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
         "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
         "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles, alu),
@@ -264,6 +267,9 @@ def run_gpu(args):
         del step, fwd_step
         torch.cuda.empty_cache()
         result["multiview"] = run_multiview(args, dev)
+    if dist_mod is not None:
+        torch.cuda.empty_cache()
+        result["sharded"] = run_sharded(args, dev, dist_mod)
     if rank == 0 and args.cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
     if dist_mod:
@@ -614,6 +620,38 @@ def run_multiview(args, dev):
             "batched_views_per_s": V / (ms_b * 1e-3), "per_view_views_per_s": V / (ms_p * 1e-3),
             "speedup": ms_p / ms_b, "batched_Mpixel_per_s": pix / (ms_b * 1e3),
             "images_identical": same, "status": st_b | st_p, "steps": args.mv_steps}
+
+
+def run_sharded(args, dev, dist_mod):
+    """The view-sharded step over the ranks of the job: config 4's cameras split across
+    the ranks (each renders its share over a full splat replica), then one all-reduce
+    (sum) of the parameter gradients over the communicator; timed with the collective
+    inside, max over ranks.  Reports the communicator's rank count."""
+    import torch
+    from paper_2406_02720_b300 import scenes
+    from paper_2406_02720_b300.rasterizer import Gaussians
+    from paper_2406_02720_b300.sharded import ShardedStep
+    sc, cams = scenes.config4(n=args.mv_n, n_views=args.mv_views)
+    dL = scenes.upstream_grad(104, cams)
+    g = Gaussians.from_scene(sc, dev)
+    step = ShardedStep(cams, g, dL, device=dev)
+    for _ in range(3):
+        step.replay()
+    torch.cuda.synchronize()
+    dist_mod.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.mv_steps):
+        step.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.mv_steps, dist_mod, dev)
+    V = len(cams)
+    return {"workload": f"config4: {sc.n} half-Gaussians, {V} cameras split over {step.world} ranks, "
+                        "fwd+bwd + one all-reduce (sum) of the parameter gradients",
+            "comm_ranks": dist_mod.get_world_size(), "backend": dist_mod.get_backend(),
+            "views_this_rank": [step.start, step.stop], "allreduce_bytes": step.flat.numel() * 4,
+            "ms_per_step": ms, "views_per_s": V / (ms * 1e-3), "status": step.status(), "steps": args.mv_steps}
 
 
 # ---- stress sweep (disks with grazing planes, 100k..6M splats) --------------------------------
