@@ -28,7 +28,7 @@ def _rank_main(rank, ws, port, out):
 def test_max_over_ranks_and_aggregate_two_gloo_ranks():
     ws = 2
     port = 29000 + os.getpid() % 1000
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)

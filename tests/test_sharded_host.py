@@ -55,7 +55,7 @@ def _rank_main(rank, ws, port, out):
 def test_gradients_summed_over_two_gloo_ranks():
     ws = 2
     port = 29500 + os.getpid() % 400
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
