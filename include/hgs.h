@@ -62,7 +62,8 @@ typedef enum {
                                  another block or warp, so none can time out    */
 #define HGS_DEV_BOUNDS 0x4    /* an index was outside its array; access skipped  */
 
-/* Half-Gaussian parameters (Sec. 3.2), activated values, [n] rows:
+/* Half-Gaussian parameters (Sec. 3.2), activated values, [n] rows; every array
+ * 16-B aligned (blocks of rows are staged with 16-byte asynchronous copies):
  *   means   [n,3]  world position mu
  *   scales  [n,3]  standard deviations (> 0), the diagonal of S in Eq. 2
  *   quats   [n,4]  rotation quaternion (w,x,y,z), any nonzero length

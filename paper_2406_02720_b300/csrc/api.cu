@@ -76,7 +76,7 @@ bool gaussians_ok(const hgs_gaussians *g) {
     if (g->n == 0) return true;
     if (!g->means || !g->scales || !g->quats || !g->normals || !g->opac1 || !g->opac2 || !g->sh) return false;
     return aligned16(g->means) && aligned16(g->scales) && aligned16(g->quats) && aligned16(g->normals) &&
-           aligned16(g->sh);
+           aligned16(g->opac1) && aligned16(g->opac2) && aligned16(g->sh);
 }
 
 bool proj_ok(const hgs_proj *p, long long vn, bool need_list = false) {

@@ -86,6 +86,29 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
+// Packed pairs of binary32 values for the paired FP32 instructions of sm_100 and
+// later (add / sub / mul .rn.f32x2 act on both halves of a 64-bit register pair at the
+// cost of one instruction).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 // One staged batch of a tile's list in shared memory, a float4 record per field
 // group so that a warp-uniform visit reads a whole group with one broadcast load.
 template <int BATCH, bool BWD>
@@ -201,11 +224,12 @@ struct Eval {
 // The per-(pixel, splat) weight of Eq. 10; true if the splat is composited
 // (a >= 1/255).  Identical instruction sequence in forward and backward.
 template <class SB>
-__device__ __forceinline__ bool eval_alpha(float fpx, float fpy, const SB &s, int k, Eval &ev) {
+__device__ __forceinline__ bool eval_alpha(f32x2 fp, const SB &s, int k, Eval &ev) {
     const float4 g0 = s.g0[k];
     const float2 g1 = *reinterpret_cast<const float2 *>(&s.g1[k]);   // u22, qcut
-    const float dx = __fsub_rn(fpx, g0.x);
-    const float dy = __fsub_rn(fpy, g0.y);
+    // pixel offset d = p - mu (both coordinates in one paired subtraction, rounded as two)
+    float dx, dy;
+    unpack2(sub2(fp, pack2(g0.x, g0.y)), dx, dy);
     const float s1 = __fmaf_rn(g0.z, dx, __fmul_rn(g0.w, dy));
     const float s2 = __fmul_rn(g1.x, dy);
     const float q = __fmaf_rn(s1, s1, __fmul_rn(s2, s2));
@@ -307,7 +331,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
     // tile-local coordinates (pixel centres at i + 1/2)
     const int ox = ti.tx * TW, oy = ti.ty * TH;
     const float fox = (float)ox, foy = (float)oy;
-    const float fpx = (float)(px - ox) + 0.5f, fpy = (float)(py - oy) + 0.5f;
+    const f32x2 fp = pack2((float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f);
     const float cxb = (float)(bx - ox) + 2.0f, cyb = (float)(by - oy) + 2.0f;   // left half's centre
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
@@ -342,7 +366,7 @@ __device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile
                 if (!done) {
                     Eval ev;
                     if (COUNT) ++c_visit;
-                    const bool hit = eval_alpha(fpx, fpy, s, k, ev);
+                    const bool hit = eval_alpha(fp, s, k, ev);
                     if (COUNT && ev.G >= 0.0f) ++c_full;
                     if (hit) {
                         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
@@ -411,7 +435,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
     // tile-local coordinates (pixel centres at i + 1/2)
     const int ox = ti.tx * TW, oy = ti.ty * TH;
     const float fox = (float)ox, foy = (float)oy;
-    const float fpx = (float)(px - ox) + 0.5f, fpy = (float)(py - oy) + 0.5f;
+    const f32x2 fp = pack2((float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f);
     const float cxb = (float)(bx - ox) + 4.0f, cyb = (float)(by - oy) + 2.0f;   // block centre
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
@@ -466,7 +490,7 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 Eval ev;
                 ev.G = -1.0f;
                 const bool cand = inside && pos < last;
-                const bool contrib = cand && eval_alpha(fpx, fpy, s, k, ev);
+                const bool contrib = cand && eval_alpha(fp, s, k, ev);
                 if (COUNT) { c_visit += cand; c_full += (cand && ev.G >= 0.0f); c_contrib += contrib; }
                 // set in full by contributing lanes only; other lanes' values are never read
                 // (the fold below selects zero for them)
@@ -526,10 +550,12 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                     if (contrib) atomic_add12(dst, gr);
                 } else {
                     if (COUNT && lane == 0) ++c_red;
+                    // lane l + 16 into lane l, two gradients per paired addition
 #pragma unroll
-                    for (int f = 0; f < 12; ++f) {
-                        const float x = contrib ? gr[f] : 0.0f;
-                        gr[f] = x + __shfl_xor_sync(0xffffffffu, x, 16);
+                    for (int f = 0; f < 12; f += 2) {
+                        const float x0 = contrib ? gr[f] : 0.0f, x1 = contrib ? gr[f + 1] : 0.0f;
+                        const f32x2 o = pack2(__shfl_xor_sync(0xffffffffu, x0, 16), __shfl_xor_sync(0xffffffffu, x1, 16));
+                        unpack2(add2(pack2(x0, x1), o), gr[f], gr[f + 1]);
                     }
                     if (lane < 16 && ((any >> lane) & 0x10001u)) atomic_add12(dst, gr);
                 }
