@@ -750,7 +750,7 @@ class OracleSample:
         self.rng = np.random.default_rng(seed)
         self.tile_order = self.rng.permutation(self.n_tiles)
         self.splat_order = self.rng.permutation(self.sc.n)
-        self.pr_full = oracle.project(self.sc, self.cam, self.tile)
+        self.pr_full = oracle.project(self.sc, self.cam, self.tile, errmat=False)
         self.bins_full = oracle.bin_pairs(self.pr_full, self.cam, self.tile)
         self.dL = np.ascontiguousarray(np.asarray(self.dL, np.float64))
         # pairs per tile from the rectangles (a 2-D difference array), to stratify the
@@ -786,7 +786,7 @@ class OracleSample:
         sub = self.sc.subset(np.sort(self.splat_order[:m]))
         g2 = np.random.default_rng(m).normal(size=(m, 12))
         t0 = time.perf_counter()
-        pr = o.project(sub, self.cam, self.tile)
+        pr = o.project(sub, self.cam, self.tile, errmat=False)
         o.bin_pairs(pr, self.cam, self.tile)
         o.project_bwd(sub, self.cam, pr["mode"], g2, self.tile)
         return time.perf_counter() - t0, pr
@@ -827,7 +827,7 @@ class OracleSample:
         o = self.oracle
         proj, bins = self._sub_problem(mask)
         t0 = time.perf_counter()
-        o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
+        o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=proj, bins=bins, margins=False)
         o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
         return time.perf_counter() - t0
 
@@ -847,7 +847,7 @@ class OracleSample:
         prep = time.perf_counter() - tb
         t_splat, _ = self._per_splat(m)
         t3 = time.perf_counter()
-        out = o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
+        out = o.render(self.sc, self.cam, tile=self.tile, tile_mask=mask, proj=proj, bins=bins, margins=False)
         o.rasterize_bwd(self.sc, self.cam, self.dL, tile=self.tile, tile_mask=mask, proj=proj, bins=bins)
         t4 = time.perf_counter()
         t0 = t3 - t_splat

@@ -216,7 +216,7 @@ def bin_pairs(proj, cam, tile=(16, 16), tile_mask=None):
 
 
 def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, tile_mask=None,
-           proj=None, bins=None, rect_mode=0, mip=False):
+           proj=None, bins=None, rect_mode=0, mip=False, margins=True):
     """Forward image: front-to-back compositing of the Eq. 10 pair weights over each
     tile's depth-sorted list (3-sigma tile culling, 1/255 floor, 0.99 clamp, 1e-4 stop).
 
@@ -227,9 +227,10 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     each the distance to the threshold over the error a binary32 evaluation can carry
     there (<= 1: FP32 cannot be expected to decide it as FP64 does); flip_img, flip_T:
     how far those decisions can move the pixel; touched [N]: splats with such a
-    decision in some pixel."""
+    decision in some pixel.  margins=False skips the error model (its outputs are then
+    absent): the render alone, as the CPU baseline times it."""
     if proj is None:
-        proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip)
+        proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip, errmat=margins)
     if bins is None:
         bins = bin_pairs(proj, cam, tile, tile_mask)
     W, H = int(cam.width), int(cam.height)
@@ -263,9 +264,12 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
                         _p(proj["conic"], dp), _p(proj["wp"], dp), _p(proj["rgb"], dp),
                         _p(proj["opac1"], dp), _p(proj["opac2"], dp), _p(ids, c_uint32),
                         _p(bins["ranges"], c_uint32), ctypes.byref(c), ctypes.byref(o), mask_p,
-                        _p(image, dp), _p(T, dp), _p(nc, c_int), _p(mg, dp), _p(mga, dp), _p(mgT, dp),
-                        _p(ncomp, c_int), em_p, _p(mgc, dp), _p(flip_img, dp), _p(flip_T, dp),
-                        _p(touched, c_ubyte))
+                        _p(image, dp), _p(T, dp), _p(nc, c_int), _p(mg, dp),
+                        _p(mga, dp) if margins else None, _p(mgT, dp) if margins else None,
+                        _p(ncomp, c_int), em_p, *((_p(mgc, dp), _p(flip_img, dp), _p(flip_T, dp), _p(touched, c_ubyte))
+                                                  if margins else (None, None, None, None)))
+    if not margins:
+        return dict(image=image, T=T, n_contrib=nc, n_comp=ncomp, proj=proj, bins=bins)
     return dict(image=image, T=T, n_contrib=nc, margin=mg, margin_a=mga, margin_T=mgT, margin_c=mgc,
                 n_comp=ncomp, flip_img=flip_img, flip_T=flip_T, touched=touched.astype(bool),
                 proj=proj, bins=bins)

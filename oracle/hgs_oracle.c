@@ -898,6 +898,8 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
     int n_tiles = tiles_x * tiles_y;
     const double u = OR_U32;
     double bgmax = fmax(fmax(fabs(cam->bg[0]), fabs(cam->bg[1])), fabs(cam->bg[2]));
+    /* the FP32 error model only when one of its outputs is wanted */
+    const int model = margin_a || margin_T || margin_c || flip_img || flip_T || touched;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int tile = 0; tile < n_tiles; ++tile) {
         if (tile_mask && !tile_mask[tile]) continue;
@@ -920,8 +922,9 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
                     double rel = fabs(e.a - OR_ALPHA_MIN) / OR_ALPHA_MIN;
                     if (rel < mg) mg = rel;
                     double band = -1.0;
-                    if (e.a >= OR_ALPHA_MIN || rel < 0.05) band = pair_band(&s, errmat, i, dx, dy, &e, o->plain, o->mip);
-                    if (rel < 0.05) {
+                    if (model && (e.a >= OR_ALPHA_MIN || rel < 0.05))
+                        band = pair_band(&s, errmat, i, dx, dy, &e, o->plain, o->mip);
+                    if (model && rel < 0.05) {
                         double na = rel / band;
                         if (na < mga) mga = na;
                         if (na <= 1.0) {          /* the floor may go either way */
@@ -931,7 +934,7 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
                             if (touched) touched[i] = 1;
                         }
                     }
-                    if (!o->plain && mode[i] == OR_STEP) {
+                    if (model && !o->plain && mode[i] == OR_STEP) {
                         /* the sign of w.d decides alpha1 or alpha2 */
                         double z = wp[2 * i] * dx + wp[2 * i + 1] * dy;
                         double zb = fabs(wp[2 * i]) * (2e-7 + u * (2.0 * fabs(dx) + 32.0)) +
@@ -956,8 +959,8 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
                     double Tn = T * (1.0 - e.a);
                     double relT = fabs(Tn - OR_T_MIN) / OR_T_MIN;
                     if (relT < mg) mg = relT;
-                    double this_err = e.a / (1.0 - e.a) * band;
-                    double nT = relT / (t_err + this_err + 2.0 * u * (ncomp + 1));
+                    double this_err = model ? e.a / (1.0 - e.a) * band : 0.0;
+                    double nT = model ? relT / (t_err + this_err + 2.0 * u * (ncomp + 1)) : 1e300;
                     if (nT < mgT) mgT = nT;
                     if (nT <= 1.0) {              /* the stop may go either way */
                         f_stop += T;
