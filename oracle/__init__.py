@@ -63,6 +63,7 @@ def lib():
                                     dp, dp, dp, dp, POINTER(c_ubyte)]
         L.or_error_basis.argtypes = [c_int, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts), ip,
                                      POINTER(c_ubyte), dp, dp]
+        L.or_pair_bands.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, c_int, c_int, c_int, ip, dp, dp, dp, dp]
         L.or_render_bwd.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, POINTER(c_uint32),
                                     POINTER(c_uint32), POINTER(OrCamera), POINTER(OrOpts),
                                     POINTER(c_ubyte), dp, dp, dp, dp]
@@ -185,6 +186,23 @@ def error_basis(sc, cam, mode, lowpass=0.3, fov_clamp=True, sel=None, scene64=No
                          _p(s["normals"], c_double), ctypes.byref(c), ctypes.byref(o), _p(mode, c_int), selp,
                          _p(E, c_double), _p(V, c_double) if vectors else None)
     return (E, V) if vectors else E
+
+
+def pair_bands(proj, ids, px, py, plain=False, mip=False):
+    """The FP32 error model's band (a bound on |ln a32 - ln a|, reading B15) and the FP64
+    pair weight before the 0.99 clamp, for splats `ids` at pixel centres (px, py);
+    band -1 where the exponent is positive."""
+    ids = np.ascontiguousarray(ids, np.int32)
+    px, py = _d(px).reshape(-1), _d(py).reshape(-1)
+    band, a = np.zeros(ids.size), np.zeros(ids.size)
+    em = proj.get("errmat")
+    em = np.ascontiguousarray(em, np.float64) if em is not None else None
+    dp = c_double
+    lib().or_pair_bands(int(proj["mode"].shape[0]), _p(np.ascontiguousarray(proj["mode"], np.int32), c_int),
+                        _p(_d(proj["mu2"]), dp), _p(_d(proj["conic"]), dp), _p(_d(proj["wp"]), dp),
+                        _p(_d(proj["opac1"]), dp), _p(_d(proj["opac2"]), dp), _p(em, dp) if em is not None else None,
+                        int(plain), int(mip), ids.size, _p(ids, c_int), _p(px, dp), _p(py, dp), _p(band, dp), _p(a, dp))
+    return band, a
 
 
 def bin_pairs(proj, cam, tile=(16, 16), tile_mask=None):

@@ -864,6 +864,27 @@ static double pair_band(const splats2d_t *s, const double *E, int i, double dx, 
     return OR_SAFETY * (shape + pos + expo + mix + rnd);
 }
 
+/* The band pair_band gives each of m (splat, pixel centre) pairs, and the FP64 pair
+ * weight a (exported for the model's pins; band -1 where the pair is past the 3-sigma
+ * exponent test, power > 0).                                                   */
+int or_pair_bands(int n, const int *mode, const double *mu2, const double *conic, const double *wp,
+                  const double *op1, const double *op2, const double *errmat, int plain, int mip, int m,
+                  const int *ids, const double *px, const double *py, double *band, double *a)
+{
+    (void)n;
+    splats2d_t s = {mode, mu2, conic, wp, NULL, op1, op2};
+    for (int j = 0; j < m; ++j) {
+        int i = ids[j];
+        eval_t e;
+        band[j] = -1.0;
+        a[j] = 0.0;
+        if (!eval_splat(&s, i, px[j], py[j], plain, &e, NULL)) continue;
+        a[j] = e.araw;
+        band[j] = pair_band(&s, errmat, i, px[j] - mu2[2 * i], py[j] - mu2[2 * i + 1], &e, plain, mip);
+    }
+    return 0;
+}
+
 /* Renders the tiles selected by tile_mask (all if NULL).
  * image [3,H,W], T [H,W], n_contrib [H,W] (1 + list position of the last
  * composited splat, 0 if none), margin [H,W] (smallest relative distance of any
