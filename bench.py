@@ -873,7 +873,51 @@ def cpu_baseline(args, m=None, k=None):
     est, meas = samp.step(m, k)
     pixels = samp.cam.width * samp.cam.height
     return {"value": pixels / (est * 1e6), "unit": "Mpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": samp.describe(m, k), "est_frame_s": est, "measured_s": meas}
+            "sample": samp.describe(m, k), "est_frame_s": est, "measured_s": meas, "cpu_model": cpu_model(),
+            "small_configs": oracle_small_configs()}
+
+
+def cpu_model():
+    """The host CPU's model name (Linux /proc/cpuinfo), or None."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_small_configs():
+    """The FP64 oracle on whole frames of the two small workloads, on one core and on all
+    cores: config 1 (1,000 splats, 64x64, forward) and config 2 (200k splats, 1280x720,
+    forward and backward), projection to parameter gradients, Mpixel/s of each."""
+    import oracle
+    from paper_2406_02720_b300 import scenes
+    cores = oracle.num_threads()
+    out = {}
+    try:
+        for name, fn, bwd in (("config1", scenes.config1, False), ("config2", scenes.config2, True)):
+            sc, cams = fn()
+            cam = cams[0]
+            dL = scenes.upstream_grad(102, cams)[0] if bwd else None
+            row = {"pixels": cam.width * cam.height, "fwd_bwd": bwd}
+            for th in (1, cores):
+                oracle.set_num_threads(th)
+                t0 = time.perf_counter()
+                pr = oracle.project(sc, cam, errmat=False)
+                bins = oracle.bin_pairs(pr, cam)
+                oracle.render(sc, cam, proj=pr, bins=bins, margins=False)
+                if bwd:
+                    g2 = oracle.rasterize_bwd(sc, cam, dL, proj=pr, bins=bins)
+                    oracle.project_bwd(sc, cam, pr["mode"], g2)
+                dt = time.perf_counter() - t0
+                row[f"s_{th}_cores"] = dt
+                row[f"Mpixel_per_s_{th}_cores"] = row["pixels"] / dt / 1e6
+            out[name] = row
+    finally:
+        oracle.set_num_threads(cores)
+    return out
 
 
 def run_reference(args):

@@ -51,6 +51,7 @@ def lib():
         dp, fp, ip = POINTER(c_double), POINTER(c_float), POINTER(c_int)
         L.or_abi_version.restype = c_int
         L.or_num_threads.restype = c_int
+        L.or_set_num_threads.argtypes = [c_int]
         L.or_project.argtypes = [c_int, dp, dp, dp, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts),
                                  ip, fp, fp, ip, ip, fp, fp, dp, dp, dp, dp, dp, dp]
         L.or_bin.argtypes = [c_int, ip, ip, fp, c_int, c_int, POINTER(c_ubyte), c_long,
@@ -79,6 +80,11 @@ def lib():
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (k >= 1)."""
+    lib().or_set_num_threads(int(k))
 
 
 def _p(a, ct):

@@ -64,6 +64,16 @@ enum { OR_CULLED = 0, OR_NORMAL = 1, OR_STEP = 2, OR_HALF = 3 };
 
 int or_abi_version(void) { return 6; }
 
+/* Threads of the OpenMP loops (the CPU baseline times one core and all cores). */
+void or_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP
