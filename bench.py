@@ -246,7 +246,8 @@ def run_gpu(args):
                    "n_splats": sc.n, "width": W, "height": H_, "views": len(cams),
                    "tile": f"{args.tile_w}x{args.tile_h}",
                    "compositing": "persistent heaviest-first queue" if args.persistent else "one block per tile",
-                   "batch": args.batch or f"{args.tile_w * args.tile_h} fwd / {min(2 * args.tile_w * args.tile_h, 512)} bwd",
+                   "batch": args.batch or (f"{args.tile_w * args.tile_h} fwd / "
+                                           f"{224 if args.tile_w * args.tile_h >= 256 else 64} bwd (3-buffer ring)"),
                    "pairs": n_pairs,
                    "parallelism": (f"replicas x{ws}" if ws == 1 else
                                    f"replicas x{ws}; view-sharded multi-view step with one gradient "

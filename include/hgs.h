@@ -58,8 +58,9 @@ typedef enum {
 
 /* bits OR-ed into *dev_status by kernels */
 #define HGS_DEV_CAPACITY 0x1  /* more (tile, splat) pairs than pair_capacity     */
-#define HGS_DEV_TIMEOUT 0x2   /* reserved: no kernel of this version waits on
-                                 another block or warp, so none can time out    */
+#define HGS_DEV_TIMEOUT 0x2   /* a bounded wait between the warps of one block
+                                 (the backward compositing pipeline) ran past
+                                 its limit (1 s); the outputs are not meaningful */
 #define HGS_DEV_BOUNDS 0x4    /* an index was outside its array; access skipped  */
 
 /* Half-Gaussian parameters (Sec. 3.2), activated values, [n] rows; every array
@@ -102,8 +103,9 @@ typedef struct {
  *   tile_w, tile_h : 8x8, 16x16 or 32x8.  The tile shape changes the image
  *                    (tiles are culled by the 3-sigma square, not per pixel).
  *   batch          : splats staged in shared memory per round: 32, 64, 128,
- *                    256 or 512 (0 = tile_w*tile_h forward and twice that,
- *                    at most 512, backward)
+ *                    224, 256 or 512 (0 = tile_w*tile_h); the backward's three
+ *                    ring buffers hold min(batch, 224) splats each (0 = 224, 64
+ *                    for 8x8 tiles)
  *   lowpass        : l added to the diagonal of hat Sigma (3D-GS uses 0.3)
  *   fov_clamp      : 1 = clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS)
  *   plain          : 1 = plain 3D-GS weight alpha1 * hat G (no half split)
@@ -267,7 +269,9 @@ hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
  *   grad2d [n_views*n, 12] (16-B aligned): d mu_x, d mu_y, d A, d B, d C,
  *          d w'_x, d w'_y, d alpha1, d alpha2, d r, d g, d b.
  * The call zeroes grad2d first.  Gradients through the 0.99 clamp, through
- * skipped or terminated splats and through P of a degenerate plane are 0. */
+ * skipped or terminated splats and through P of a degenerate plane are 0.
+ * Within a block, one warp stages each tile's list in batches and the others walk
+ * them, synchronised by bounded waits: HGS_DEV_TIMEOUT if one runs out. */
 hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids,
                              const uint32_t *ranges, const hgs_camera *cams_host,
                              const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
@@ -323,6 +327,13 @@ hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, co
  * argument (nothing enqueued). */
 hgs_status hgs_probe_peak(int kind, int blocks_per_sm, int iters, float *sink, double *lane_ops,
                           void *stream);
+
+/* Self-test of the bounded wait of the backward compositing pipeline
+ * (hgs_rasterize_bwd; the paper has no counterpart).  One warp waits on a shared-memory mbarrier that nothing completes;
+ * the wait ends at its bound (about 1 s), HGS_DEV_TIMEOUT is OR-ed into
+ * *dev_status and the kernel returns, so the device stays usable.  HGS_ERR_INVALID
+ * if dev_status is NULL (nothing enqueued). */
+hgs_status hgs_selftest_wait(int *dev_status, void *stream);
 
 /* ---- misc ------------------------------------------------------------------- */
 const char *hgs_status_string(hgs_status s);

@@ -173,6 +173,11 @@ hgs_status hgs_bin(const hgs_proj *proj, int n, const hgs_camera *cams_host, int
     return cuda_status(launch_bin(p, static_cast<cudaStream_t>(stream)));
 }
 
+hgs_status hgs_selftest_wait(int *dev_status, void *stream) {
+    if (!dev_status) return HGS_ERR_INVALID;
+    return cuda_status(launch_wait_selftest(dev_status, static_cast<cudaStream_t>(stream)));
+}
+
 static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                                 const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                                 const hgs_config *cfg, void *ws, size_t ws_bytes, RenderLaunch *p) {

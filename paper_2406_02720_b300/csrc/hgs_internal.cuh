@@ -101,6 +101,7 @@ struct RenderLaunch {
 size_t render_workspace_bytes(const ViewTable &vt, const hgs_config &cfg);
 cudaError_t launch_render_fwd(const RenderLaunch &p, cudaStream_t s);
 cudaError_t launch_render_bwd(const RenderLaunch &p, cudaStream_t s);
+cudaError_t launch_wait_selftest(int *status, cudaStream_t s);
 
 int num_sms();
 

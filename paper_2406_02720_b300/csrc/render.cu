@@ -2,7 +2,8 @@
 //
 // Blocks walk a tile's depth-sorted list in batches that they stage in shared
 // memory (the forward uses two 128-thread blocks per 16x16 tile, one per 16x8
-// half; the backward one 256-thread block).  For each (pixel, splat) pair:
+// half; the backward one block of 256 pixel threads and a staging warp).  For each
+// (pixel, splat) pair:
 //   d = p - mu-hat,  hat G = exp(-1/2 |U d|^2), conic = U^T U  (Eq. 4-5)
 //   P = 1/2 erfc(-w'.d)                                         (Eq. 7-8)
 //   a = min(0.99, (alpha2 + (alpha1 - alpha2) P) hat G)          (Eq. 10)
@@ -30,7 +31,10 @@
 // inflated past the cut-off, so culling changes no per-pixel decision.
 //
 // The backward walks each pixel's list back to front from its last composited
-// splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i).
+// splat, rebuilding the transmittance by division, T_i = T_{i+1} / (1 - a_i).  Its
+// warps are not held together by block barriers: a staging warp fills a ring of
+// three batch buffers and each pixel warp walks them at its own pace (mbarriers,
+// bounded waits; 1.318 -> 1.294 ms against block-synchronous batches).
 // The 12 screen-space gradients of a (warp, splat) leave as per-lane float4
 // atomic adds, with one shuffle level folding lane pairs first when more than 16
 // lanes contribute.
@@ -299,6 +303,13 @@ __device__ __forceinline__ TileInfo tile_info(const RenderLaunch &p, int gtile) 
     return ti;
 }
 
+// Work queue of the persistent kernels (k_queue_count / k_queue_fill build the order).
+struct Queue {
+    uint32_t counter_fwd, counter_bwd;
+    uint32_t bucket_count[33];
+    uint32_t bucket_cursor[33];
+};
+
 // ---- forward -------------------------------------------------------------------------
 // Pixel of a thread: warp w covers the 8x4 block (w % (TW/8), w / (TW/8)) of the tile.
 // With SPLIT blocks per tile, block `part` covers rows [part, part + 1) * TH / SPLIT.
@@ -421,62 +432,187 @@ __device__ __forceinline__ void atomic_add12(float *dst, const float g[12]) {
     atomicAdd(d4 + 2, make_float4(g[8], g[9], g[10], g[11]));
 }
 
-template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
-__device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH, true> &s,
-                                                uint32_t &s_maxlast) {
-    constexpr int SPLIT = kSplit<false, TW, TH>;
-    constexpr int NT = TW * TH / SPLIT;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const TileInfo ti = tile_info<TW, TH>(p, gtile);
-    int bx, by;
-    warp_block<TW>(ti, TH, part * (TH / SPLIT), bx, by);
-    const int px = bx + (lane & 7), py = by + (lane >> 3);
-    const bool inside = px < ti.W && py < ti.H;
-    // tile-local coordinates (pixel centres at i + 1/2)
-    const int ox = ti.tx * TW, oy = ti.ty * TH;
-    const float fox = (float)ox, foy = (float)oy;
-    const f32x2 fp = pack2((float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f);
-    const float cxb = (float)(bx - ox) + 4.0f, cyb = (float)(by - oy) + 2.0f;   // block centre
+// The backward runs as a pipeline with no block barriers.  One producer warp takes
+// tiles from the queue, finds each tile's list end (the latest last contributor of
+// its pixels, from n_contrib) and stages the list back to front in batches into a
+// ring of kBwdStages shared buffers; each of the TW*TH/32 consumer warps walks the
+// batches in order at its own pace.  A buffer's "full" mbarrier completes when the
+// producer has staged it, its "empty" mbarrier when every consumer warp has walked
+// it, so the consumers wait only for staging and the producer only for the slowest
+// consumer, NB - 1 batches behind, across tile boundaries too.  Every wait is
+// bounded: after kWaitNs the waiting warp sets HGS_DEV_TIMEOUT and leaves, and the
+// others' waits then run out in turn, so the kernel always ends.
+constexpr int kBwdStages = 3;
+
+struct BwdHeader {
+    int gtile;                  // < 0: no more work
+    uint32_t bstart, bend;      // the batch's slice of the tile's list
+    int first;                  // first batch of its tile (the one nearest the list end)
+};
+
+template <int BATCH>
+struct BwdRing {
+    Batch<BATCH, true> buf[kBwdStages];
+    BwdHeader hdr[kBwdStages];
+    unsigned long long full[kBwdStages], empty[kBwdStages];   // mbarriers
+};
+
+constexpr unsigned long long kWaitNs = 1000ull * 1000 * 1000;   // 1 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase of the given parity to complete; false (and HGS_DEV_TIMEOUT) if
+// it has not after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *status) {
+    const uint32_t addr = smem_addr(bar);
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (i == 0) t0 = global_ns();
+        if ((i & 63u) == 63u && global_ns() - t0 > kWaitNs) {
+            set_status(status, HGS_DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Producer warp: tiles from the queue (or this block's tile), batches back to front.
+template <int TW, int TH, int BATCH, bool PLAIN>
+__device__ void bwd_produce(const RenderLaunch &p, BwdRing<BATCH> &r) {
+    constexpr int NB = kBwdStages;
+    const int lane = threadIdx.x & 31;
     const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
     const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
-    const size_t HW = (size_t)ti.W * ti.H;
-    const size_t pix = (size_t)py * ti.W + px;
-    float T = 1.0f, Tf = 1.0f, g0_ = 0, g1_ = 0, g2_ = 0;
-    uint32_t last = 0;
-    if (inside) {
-        Tf = p.final_T[ti.pix_off + pix];
-        last = p.n_contrib[ti.pix_off + pix];
-        const float *gi = p.dL_dimage + 3 * (size_t)ti.pix_off;
-        g0_ = gi[pix]; g1_ = gi[HW + pix]; g2_ = gi[2 * HW + pix];
-        T = Tf;
+    Queue *qw = reinterpret_cast<Queue *>(p.ws);
+    const uint32_t *order = reinterpret_cast<const uint32_t *>(qw + 1);
+    uint32_t seq = 0;
+    for (int round = 0;; ++round) {
+        int gtile = -1;
+        if (p.cfg.persistent) {
+            uint32_t item = 0;
+            if (lane == 0) item = atomicAdd(&qw->counter_bwd, 1u);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item < (uint32_t)p.vt.total_tiles) gtile = (int)order[item];
+        } else if (round == 0) {
+            gtile = (int)blockIdx.x;
+        }
+        const uint32_t slot0 = seq % NB;
+        if (gtile < 0) {
+            // end marker in the next buffer
+            if (seq >= NB && !mbar_wait(&r.empty[slot0], ((seq / NB) - 1) & 1u, p.status)) return;
+            if (lane == 0) r.hdr[slot0].gtile = -1;
+            __syncwarp();
+            mbar_arrive(&r.full[slot0]);
+            return;
+        }
+        const TileInfo ti = tile_info<TW, TH>(p, gtile);
+        // the tile's list end: the latest last contributor of its pixels
+        const int ox = ti.tx * TW, oy = ti.ty * TH;
+        uint32_t ml = 0;
+        for (int i = lane; i < TW * TH; i += 32) {
+            const int px = ox + (i % TW), py = oy + (i / TW);
+            if (px < ti.W && py < ti.H) ml = max(ml, p.n_contrib[ti.pix_off + (size_t)py * ti.W + px]);
+        }
+        ml = __reduce_max_sync(0xffffffffu, ml);
+        const uint32_t tile_end = min(ti.end, ti.beg + ml);
+        const float fox = (float)ox, foy = (float)oy;
+        for (uint32_t bend = tile_end; bend > ti.beg;) {
+            const uint32_t bstart = (bend - ti.beg > (uint32_t)BATCH) ? bend - BATCH : ti.beg;
+            const uint32_t slot = seq % NB;
+            if (seq >= NB && !mbar_wait(&r.empty[slot], ((seq / NB) - 1) & 1u, p.status)) return;
+            Batch<BATCH, true> &sb = r.buf[slot];
+            for (int k = lane; k < BATCH; k += 32) {
+                const uint32_t j = bstart + k;
+                if (j < bend) {
+                    uint32_t id = p.ids[j];
+                    if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
+                    stage<BATCH, true>(rec, id, sb, k, fox, foy, PLAIN);
+                }
+            }
+            if (lane == 0) {
+                r.hdr[slot].gtile = gtile;
+                r.hdr[slot].bstart = bstart;
+                r.hdr[slot].bend = bend;
+                r.hdr[slot].first = bend == tile_end;
+            }
+            __syncwarp();
+            mbar_arrive(&r.full[slot]);           // each lane: its staged slots are released
+            ++seq;
+            bend = bstart;
+        }
     }
-    const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
-    if (tid == 0) s_maxlast = 0;
-    __syncthreads();
-    if (lane == 0 && wlast) atomicMax(&s_maxlast, wlast);
-    __syncthreads();
-    const uint32_t tile_end = min(ti.end, ti.beg + s_maxlast);
-    const float bgg = ti.bg[0] * g0_ + ti.bg[1] * g1_ + ti.bg[2] * g2_;
-    const float TfB = Tf * bgg;             // d L / d a_i gets -T_final bg.g / (1 - a_i)
+}
+
+// Consumer warp: walks each batch for its 8x4 pixel block, back to front.
+template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
+__device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH> &r) {
+    constexpr int NB = kBwdStages;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr bool plain = PLAIN;
-    // colour composited behind the current splat, dotted with this pixel's dL/dC:
-    // (c_i - S_i).g = c_i.g - S_i.g, and S.g follows the same recurrence as S
-    float Sg = 0.0f;
     float *grad = p.grad2d;
     unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0;
-    for (uint32_t bend = tile_end; bend > ti.beg;) {
-        const uint32_t bstart = (bend - ti.beg > (uint32_t)BATCH) ? bend - BATCH : ti.beg;
-        __syncthreads();
-        for (int k = tid; k < BATCH; k += NT) {
-            const uint32_t j = bstart + k;
-            if (j < bend) {
-                uint32_t id = p.ids[j];
-                if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH, true>(rec, id, s, k, fox, foy, plain);
+    // per-tile state of this lane's pixel
+    bool inside = false;
+    f32x2 fp = 0;
+    float cxb = 0.0f, cyb = 0.0f, T = 1.0f, g0_ = 0.0f, g1_ = 0.0f, g2_ = 0.0f, TfB = 0.0f, Sg = 0.0f;
+    uint32_t last = 0, wlast = 0, beg = 0;
+    for (uint32_t seq = 0;; ++seq) {
+        const uint32_t slot = seq % NB;
+        if (!mbar_wait(&r.full[slot], (seq / NB) & 1u, p.status)) break;
+        const BwdHeader h = r.hdr[slot];
+        if (h.gtile < 0) break;
+        const Batch<BATCH, true> &s = r.buf[slot];
+        if (h.first) {
+            const TileInfo ti = tile_info<TW, TH>(p, h.gtile);
+            const int bx = ti.tx * TW + (warp % (TW / 8)) * 8, by = ti.ty * TH + (warp / (TW / 8)) * 4;
+            const int px = bx + (lane & 7), py = by + (lane >> 3);
+            inside = px < ti.W && py < ti.H;
+            const int ox = ti.tx * TW, oy = ti.ty * TH;
+            fp = pack2((float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f);
+            cxb = (float)(bx - ox) + 4.0f;
+            cyb = (float)(by - oy) + 2.0f;   // block centre
+            const size_t HW = (size_t)ti.W * ti.H;
+            const size_t pix = (size_t)py * ti.W + px;
+            float Tf = 1.0f;
+            g0_ = g1_ = g2_ = 0.0f;
+            last = 0;
+            if (inside) {
+                Tf = p.final_T[ti.pix_off + pix];
+                last = p.n_contrib[ti.pix_off + pix];
+                const float *gi = p.dL_dimage + 3 * (size_t)ti.pix_off;
+                g0_ = gi[pix]; g1_ = gi[HW + pix]; g2_ = gi[2 * HW + pix];
             }
+            T = Tf;
+            wlast = __reduce_max_sync(0xffffffffu, last);
+            const float bgg = ti.bg[0] * g0_ + ti.bg[1] * g1_ + ti.bg[2] * g2_;
+            TfB = Tf * bgg;             // d L / d a_i gets -T_final bg.g / (1 - a_i)
+            // colour composited behind the current splat, dotted with this pixel's dL/dC:
+            // (c_i - S_i).g = c_i.g - S_i.g, and S.g follows the same recurrence as S
+            Sg = 0.0f;
+            beg = ti.beg;
         }
-        __syncthreads();
-        const uint32_t rel0 = bstart - ti.beg;
+        const uint32_t bstart = h.bstart, bend = h.bend;
+        const uint32_t rel0 = bstart - beg;
         // this warp's part of the batch: nothing at or past its pixels' last splat
         const int cnt = (int)min(bend - bstart, wlast > rel0 ? wlast - rel0 : 0u);
         for (int c = (cnt - 1) & ~31; c >= 0; c -= 32) {
@@ -561,24 +697,18 @@ __device__ __forceinline__ void render_tile_bwd(const RenderLaunch &p, int gtile
                 }
             }
         }
-        bend = bstart;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&r.empty[slot]);
     }
     if (COUNT) add_counters(p.counters + 3, c_visit, c_full, c_contrib, c_red);
 }
 
 // ---- kernels ------------------------------------------------------------------------
-// Resident blocks per SM asked of the register allocator, in eighths of the SM's
-// 64 warps: forward 5/8 (at most 48 registers a thread), backward 4/8.  Measured
-// at 3M splats, 1080p: the forward gains ~3% from the extra block, the backward
-// loses ~8% to the spills that 48 registers cost it.
+// Resident blocks per SM asked of the register allocator for the forward, in eighths
+// of the SM's 64 warps: 5/8 (at most 48 registers a thread; measured at 3M splats,
+// 1080p, ~3% faster than 4/8).
 template <int NT, int EIGHTHS>
 constexpr int kMinBlocks = 2048 / NT * EIGHTHS / 8;
-
-struct Queue {
-    uint32_t counter_fwd, counter_bwd;
-    uint32_t bucket_count[33];
-    uint32_t bucket_cursor[33];
-};
 
 template <int TW, int TH, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / kSplit<true, TW, TH>, (kMinBlocks<TW * TH / kSplit<true, TW, TH>, 5>))
@@ -602,27 +732,28 @@ __global__ void __launch_bounds__(TW *TH / kSplit<true, TW, TH>, (kMinBlocks<TW 
     }
 }
 
+// Backward: TW*TH consumer threads (one pixel each) and one producer warp; resident
+// blocks asked of the register allocator: 4 of 288 threads (56 registers) for 16x16 and
+// 32x8 tiles, 10 of 96 for 8x8.
+template <int TW, int TH>
+constexpr int kBwdMinBlocks = TW * TH >= 256 ? 4 : 10;
+
 template <int TW, int TH, int BATCH, bool COUNT, bool PLAIN>
-__global__ void __launch_bounds__(TW *TH / kSplit<false, TW, TH>, (kMinBlocks<TW * TH / kSplit<false, TW, TH>, 4>))
-    k_render_bwd(RenderLaunch p) {
-    constexpr int SPLIT = kSplit<false, TW, TH>;
-    __shared__ Batch<BATCH, true> s;
-    __shared__ uint32_t s_maxlast;
-    if (!p.cfg.persistent) {
-        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, blockIdx.x / SPLIT, blockIdx.x % SPLIT, s, s_maxlast);
-        return;
+__global__ void __launch_bounds__(TW *TH + 32, (kBwdMinBlocks<TW, TH>)) k_render_bwd(RenderLaunch p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdRing<BATCH> &r = *reinterpret_cast<BwdRing<BATCH> *>(smem_raw);
+    constexpr int NB = kBwdStages, NC = TW * TH;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&r.full[i], 32);          // the producer warp's lanes
+            mbar_init(&r.empty[i], NC / 32);    // one arrival per consumer warp
+        }
     }
-    Queue *q = reinterpret_cast<Queue *>(p.ws);
-    const uint32_t *order = reinterpret_cast<const uint32_t *>(q + 1);
-    __shared__ uint32_t s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&q->counter_bwd, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= (uint32_t)p.vt.total_tiles * SPLIT) break;
-        render_tile_bwd<TW, TH, BATCH, COUNT, PLAIN>(p, (int)order[item / SPLIT], (int)(item % SPLIT), s, s_maxlast);
-        __syncthreads();
-    }
+    __syncthreads();
+    if (threadIdx.x >= NC)
+        bwd_produce<TW, TH, BATCH, PLAIN>(p, r);
+    else
+        bwd_consume<TW, TH, BATCH, COUNT, PLAIN>(p, r);
 }
 
 // Work order for the persistent kernels: tiles bucketed by floor(log2(list length)),
@@ -667,12 +798,27 @@ __global__ void k_queue_fill(const uint32_t *ranges, int total_tiles, Queue *q, 
 }
 
 template <int TW, int TH, int BATCH, bool FWD, bool COUNT, bool PLAIN>
+constexpr auto render_kernel() {
+    if constexpr (FWD)
+        return k_render_fwd<TW, TH, BATCH, COUNT>;
+    else
+        return k_render_bwd<TW, TH, BATCH, COUNT, PLAIN>;
+}
+
+template <int TW, int TH, int BATCH, bool FWD, bool COUNT, bool PLAIN>
 cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
-    auto kern = FWD ? k_render_fwd<TW, TH, BATCH, COUNT> : k_render_bwd<TW, TH, BATCH, COUNT, PLAIN>;
-    constexpr int SPLIT = kSplit<FWD, TW, TH>, NT = TW * TH / SPLIT;
+    auto kern = render_kernel<TW, TH, BATCH, FWD, COUNT, PLAIN>();
+    constexpr int SPLIT = kSplit<FWD, TW, TH>, NT = FWD ? TW * TH / SPLIT : TW * TH + 32;
+    constexpr int smem = FWD ? 0 : (int)sizeof(BwdRing<FWD ? 32 : BATCH>);
     const int items = p.vt.total_tiles * SPLIT;
+    if (smem > 48 * 1024) {
+        // above the default dynamic shared-memory limit; a per-device attribute, so set
+        // on every call (a host-side call, no stream work)
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
     if (!p.cfg.persistent) {
-        kern<<<items, NT, 0, s>>>(p);
+        kern<<<items, NT, smem, s>>>(p);
         return cudaGetLastError();
     }
     // resident blocks per SM (assumed the same on every device of this architecture: the
@@ -681,11 +827,11 @@ cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
     static std::atomic<int> occ_cache{0};
     int occ = occ_cache.load(std::memory_order_relaxed);
     if (!occ) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
         occ = std::max(occ, 1);
         occ_cache.store(occ, std::memory_order_relaxed);
     }
-    kern<<<std::min(num_sms() * occ, items), NT, 0, s>>>(p);
+    kern<<<std::min(num_sms() * occ, items), NT, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -713,17 +859,28 @@ cudaError_t prepare_queue(const RenderLaunch &p, cudaStream_t s) {
 // dispatch over the supported (tile shape, batch) combinations
 template <bool FWD, int TW, int TH>
 cudaError_t dispatch_batch(const RenderLaunch &p, cudaStream_t s) {
-    // default: the tile's pixel count forward, twice that backward (capped at 512), where
-    // longer batches average out the uneven per-warp work between block barriers
-    // (16x16 tiles at 3M splats: forward 0.677 / 0.697 / 0.886 ms at 256 / 128 / 512;
-    // backward 1.48 at 512 vs 1.50 at 256 in an earlier version of the kernel)
-    const int batch = p.cfg.batch ? p.cfg.batch : (FWD ? TW * TH : std::min(2 * TW * TH, 512));
-    switch (batch) {
-        case 32: return launch_c<TW, TH, 32, FWD>(p, s);
-        case 64: return launch_c<TW, TH, 64, FWD>(p, s);
-        case 128: return launch_c<TW, TH, 128, FWD>(p, s);
-        case 256: return launch_c<TW, TH, 256, FWD>(p, s);
-        case 512: return launch_c<TW, TH, 512, FWD>(p, s);
+    if (FWD) {
+        // default: the tile's pixel count (16x16 tiles at 3M splats: forward 0.677 / 0.697 /
+        // 0.886 ms at 256 / 128 / 512)
+        switch (p.cfg.batch ? p.cfg.batch : TW * TH) {
+            case 32: return launch_c<TW, TH, 32, true>(p, s);
+            case 64: return launch_c<TW, TH, 64, true>(p, s);
+            case 128: return launch_c<TW, TH, 128, true>(p, s);
+            case 224: return launch_c<TW, TH, 224, true>(p, s);
+            case 256: return launch_c<TW, TH, 256, true>(p, s);
+            case 512: return launch_c<TW, TH, 512, true>(p, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    // backward: ring buffers of at most 224 splats, so that the three of them leave room
+    // for 4 blocks per SM (3 x 256 splats: 3 blocks, backward 1.29 -> 1.37 ms); default
+    // 224, 64 for 8x8 tiles
+    const int req = p.cfg.batch ? p.cfg.batch : (TW * TH >= 256 ? 224 : 64);
+    switch (std::min(req, 224)) {
+        case 32: return launch_c<TW, TH, 32, false>(p, s);
+        case 64: return launch_c<TW, TH, 64, false>(p, s);
+        case 128: return launch_c<TW, TH, 128, false>(p, s);
+        case 224: return launch_c<TW, TH, 224, false>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -742,7 +899,21 @@ cudaError_t dispatch(const RenderLaunch &p, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// Self-test of the bounded wait the backward pipeline uses: one warp waits on an
+// mbarrier that nothing arrives at, until the wait's bound ends it (HGS_DEV_TIMEOUT).
+__global__ void k_wait_selftest(int *status) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncwarp();
+    mbar_wait(&bar, 0, status);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(int *status, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
+}
 
 size_t render_workspace_bytes(const ViewTable &vt, const hgs_config &cfg) {
     (void)cfg;

@@ -103,6 +103,8 @@ def lib():
                                      _CFG_P, vp, c_size_t, vp, vp, vp, vp, POINTER(HgsGaussianGrads), vp, vp]
         L.hgs_probe_peak.restype = c_int
         L.hgs_probe_peak.argtypes = [c_int, c_int, c_int, vp, POINTER(ctypes.c_double), vp]
+        L.hgs_selftest_wait.restype = c_int
+        L.hgs_selftest_wait.argtypes = [vp, vp]
         _LIB = L
     return _LIB
 
@@ -206,6 +208,12 @@ def hgs_probe_peak(kind, blocks_per_sm, iters, sink, stream) -> float:
     ops = ctypes.c_double(0.0)
     _check(lib().hgs_probe_peak(kind, blocks_per_sm, iters, sink, ctypes.byref(ops), stream), "hgs_probe_peak")
     return ops.value
+
+
+def hgs_selftest_wait(dev_status, stream):
+    """Enqueues a wait that nothing ends: it runs out at its bound and sets
+    HGS_DEV_TIMEOUT in *dev_status."""
+    _check(lib().hgs_selftest_wait(dev_status, stream), "hgs_selftest_wait")
 
 
 STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd_contrib", "bwd_warp_red"]
