@@ -74,6 +74,7 @@ def lib():
                                     dp, dp, dp, dp]
         L.or_eval_splat.restype = c_int
         L.or_sh_eval.argtypes = [c_int, c_int, dp, dp]
+        L.or_alg1_flat_cov.argtypes = [dp, dp, dp]
         _LIB = L
     return _LIB
 
@@ -142,7 +143,8 @@ def grid(cam, tile):
 def project(sc, cam, tile=(16, 16), lowpass=0.3, fov_clamp=True, rect_mode=0, mip=False, errmat=True,
             err_sel=None):
     """Per-splat projection (Eq. 2-5, 7-8; SH colour), plus canonical binning fields.
-    rect_mode 0: the 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4).
+    rect_mode 0: the 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4);
+    2: the same with the splitting edge from Algorithm 1's flattened covariance.
     mip: the low-pass as Mip-Splatting's mass-preserving 2D filter; "opac1"/"opac2" are
     then the compensated opacities the compositing uses ("comp" holds the factor).
     errmat: also the FP32 error model's per-splat matrix "errmat" [N,15] (see
@@ -447,3 +449,14 @@ def loss_and_grads(sc, cam, dL_dimage, **kw):
 
 def so_path() -> str:
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "liborhgs.so")
+
+
+def alg1_flat_cov(Sigma, n):
+    """Algorithm 1 (Suppl. B.1) in FP64: the covariance of the flattened ellipsoid that
+    holds the cut of the Gaussian of covariance Sigma (3x3) by the plane through its
+    mean with normal n (3,)."""
+    S = _d(Sigma).reshape(9)
+    nv = _d(n).reshape(3)
+    out = np.zeros(9, np.float64)
+    lib().or_alg1_flat_cov(_p(S, c_double), _p(nv, c_double), _p(out, c_double))
+    return out.reshape(3, 3)

@@ -50,7 +50,9 @@ typedef struct {
     int sh_degree;
     int fov_clamp;   /* 1: clamp x/z, y/z to +-1.3 tan(fov/2) inside J (3D-GS convention) */
     int plain;       /* 1: plain 3D-GS, alpha = alpha1 * hat G (P unused)           */
-    int rect_mode;   /* 0: 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4) */
+    int rect_mode;   /* 0: 3-sigma square of 3D-GS; 1: per-half 3-sigma extents (Sec. 3.4);
+                        2: the same with the splitting edge from Algorithm 1's flattened
+                        covariance (Suppl. B.1) instead of the exact cut ellipse */
     int mip;         /* 1: the low-pass is a mass-preserving 2D filter (Mip-Splatting-HGS):
                         both opacities scale by sqrt(det hat Sigma_0 / det hat Sigma)   */
     double lowpass;  /* l added to the diagonal of hat Sigma (3D-GS uses 0.3)        */
@@ -62,7 +64,58 @@ enum { OR_CULLED = 0, OR_NORMAL = 1, OR_STEP = 2, OR_HALF = 3 };
 #define OR_ALPHA_MAX 0.99
 #define OR_T_MIN 1e-4
 
-int or_abi_version(void) { return 6; }
+int or_abi_version(void) { return 7; }
+
+/* Algorithm 1 (Suppl. B.1), step by step in binary64: the covariance `out` (3x3,
+ * row-major) of the flattened ellipsoid that holds the cut of the Gaussian of
+ * covariance Sigma (3x3, row-major) by the plane through its mean with normal n.
+ * The basis (v1, v2, n^) has the plane's two directions first; in it, the in-plane
+ * 2x2 block is the covariance given the normal coordinate (a', b', c'), and the third
+ * axis keeps a variance of min(a', c') / 100; the result is rotated back. */
+void or_alg1_flat_cov(const double *Sigma, const double *n, double *out) {
+    double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double h[3] = {n[0] / nl, n[1] / nl, n[2] / nl};
+    double v1[3], v2[3];
+    if (h[0] == 0.0 && h[1] == 0.0) {
+        v1[0] = 1.0; v1[1] = 0.0; v1[2] = 0.0;
+        v2[0] = 0.0; v2[1] = 1.0; v2[2] = 0.0;
+    } else {
+        double l1 = sqrt(h[1] * h[1] + h[0] * h[0]);
+        v1[0] = h[1] / l1; v1[1] = -h[0] / l1; v1[2] = 0.0;
+        double c[3] = {h[1] * v1[2] - h[2] * v1[1], h[2] * v1[0] - h[0] * v1[2], h[0] * v1[1] - h[1] * v1[0]};
+        double l2 = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        for (int i = 0; i < 3; ++i) v2[i] = c[i] / l2;
+    }
+    double B[3][3];                     /* columns v1, v2, n^ */
+    for (int i = 0; i < 3; ++i) { B[i][0] = v1[i]; B[i][1] = v2[i]; B[i][2] = h[i]; }
+    double SB[3][3], cov[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            SB[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k) SB[i][j] += Sigma[3 * i + k] * B[k][j];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cov[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k) cov[i][j] += B[k][i] * SB[k][j];
+        }
+    double ap = cov[0][0] - cov[0][2] * cov[0][2] / cov[2][2];
+    double bp = cov[0][1] - cov[0][2] * cov[1][2] / cov[2][2];
+    double cp = cov[1][1] - cov[1][2] * cov[1][2] / cov[2][2];
+    double sl[3][3] = {{ap, bp, 0.0}, {bp, cp, 0.0}, {0.0, 0.0, fmin(ap, cp) / 100.0}};
+    double T[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k) T[i][j] += B[i][k] * sl[k][j];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += T[i][k] * B[j][k];
+            out[3 * i + j] = acc;
+        }
+}
 
 /* Threads of the OpenMP loops (the CPU baseline times one core and all cores). */
 void or_set_num_threads(int k)
@@ -218,7 +271,7 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
 
     /* 15. extents towards -x, +x, -y, +y: the 3-sigma radius r (3D-GS), or per half */
     float ex0 = r, ex1 = r, ey0 = r, ey1 = r;
-    if (o->rect_mode == 1) {
+    if (o->rect_mode == 1 || o->rect_mode == 2) {
         /* 15a. Support of the 3-sigma half-ellipsoid {|L^-1 (x - mu)| <= 3, n.(x - mu) >= 0}
          * under the affine projection M, in direction e (1-sigma, without the low-pass):
          * sqrt(e^T P P^T e) if the whole ellipsoid's extreme point in that direction lies on
@@ -247,9 +300,79 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
             K1 = P[1][0] * u[0];
             K1 = K1 + P[1][1] * u[1];
             K1 = K1 + P[1][2] * u[2];
-            if (vs > 0.0f) {
+            if (vs > 0.0f && o->rect_mode == 1) {
                 Ar = fmaxf(0.0f, A0 - (K0 * K0) / vs);
                 Cr = fmaxf(0.0f, C0 - (K1 * K1) / vs);
+            } else if (vs > 0.0f) {
+                /* 15a'. Algorithm 1 (Suppl. B.1) in binary32: basis (v1, v2, n^) of the
+                 * splitting plane, the covariance in that basis from the rows L^T v1,
+                 * L^T v2, L^T n^ (= u), the in-plane covariance given the normal
+                 * coordinate (a', b', c'), a third variance min(a', c') / 100 along n^,
+                 * and the projection M sigma M^T of the resulting flattened covariance,
+                 * whose diagonal replaces the cut ellipse's (Ar, Cr).                    */
+                float v1[3], v2[3];
+                if (h0 == 0.0f && h1 == 0.0f) {
+                    v1[0] = 1.0f; v1[1] = 0.0f; v1[2] = 0.0f;
+                    v2[0] = 0.0f; v2[1] = 1.0f; v2[2] = 0.0f;
+                } else {
+                    float l1 = h1 * h1;
+                    l1 = l1 + h0 * h0;
+                    l1 = sqrtf(l1);
+                    v1[0] = h1 / l1; v1[1] = -(h0 / l1); v1[2] = 0.0f;
+                    float c0 = -(h2 * v1[1]);             /* n^ x v1 with v1[2] = 0 */
+                    float c1 = h2 * v1[0];
+                    float c2 = h0 * v1[1];
+                    c2 = c2 - h1 * v1[0];
+                    float l2 = c0 * c0;
+                    l2 = l2 + c1 * c1;
+                    l2 = l2 + c2 * c2;
+                    l2 = sqrtf(l2);
+                    v2[0] = c0 / l2; v2[1] = c1 / l2; v2[2] = c2 / l2;
+                }
+                float g1[3], g2[3];
+                for (int k = 0; k < 3; ++k) {
+                    float acc = L[0][k] * v1[0];
+                    acc = acc + L[1][k] * v1[1];
+                    g1[k] = acc + L[2][k] * v1[2];
+                    acc = L[0][k] * v2[0];
+                    acc = acc + L[1][k] * v2[1];
+                    g2[k] = acc + L[2][k] * v2[2];
+                }
+                float s00 = g1[0] * g1[0], s01 = g1[0] * g2[0], s11 = g2[0] * g2[0];
+                float s02 = g1[0] * u[0], s12 = g2[0] * u[0];
+                for (int k = 1; k < 3; ++k) {
+                    s00 = s00 + g1[k] * g1[k];
+                    s01 = s01 + g1[k] * g2[k];
+                    s11 = s11 + g2[k] * g2[k];
+                    s02 = s02 + g1[k] * u[k];
+                    s12 = s12 + g2[k] * u[k];
+                }
+                float ap = s00 - (s02 * s02) / vs;
+                float bp = s01 - (s02 * s12) / vs;
+                float cp = s11 - (s12 * s12) / vs;
+                float tt = fminf(ap, cp) / 100.0f;
+                float q[2][3];
+                for (int i = 0; i < 2; ++i) {
+                    float acc = M[i][0] * v1[0];
+                    acc = acc + M[i][1] * v1[1];
+                    q[i][0] = acc + M[i][2] * v1[2];
+                    acc = M[i][0] * v2[0];
+                    acc = acc + M[i][1] * v2[1];
+                    q[i][1] = acc + M[i][2] * v2[2];
+                    acc = M[i][0] * h0;
+                    acc = acc + M[i][1] * h1;
+                    q[i][2] = acc + M[i][2] * h2;
+                }
+                float As = ap * (q[0][0] * q[0][0]);
+                As = As + (2.0f * bp) * (q[0][0] * q[0][1]);
+                As = As + cp * (q[0][1] * q[0][1]);
+                As = As + tt * (q[0][2] * q[0][2]);
+                float Cs = ap * (q[1][0] * q[1][0]);
+                Cs = Cs + (2.0f * bp) * (q[1][0] * q[1][1]);
+                Cs = Cs + cp * (q[1][1] * q[1][1]);
+                Cs = Cs + tt * (q[1][2] * q[1][2]);
+                Ar = fmaxf(0.0f, As);
+                Cr = fmaxf(0.0f, Cs);
             }
         }
         /* 15b. a half is splatted when its opacity reaches the 1/255 floor (as binary32) */
