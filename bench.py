@@ -260,7 +260,8 @@ def run_gpu(args):
         "e2e": e2e, "e2e_params_over_pcie": e2e_full, "gpu_launches": launches * args.steps,
     }
     if args.rect_modes:
-        result["rect_mode_1"] = run_rect_mode1(args, dev, g, dL, rast, n_pairs)
+        result["rect_mode_1"] = run_rect_mode(args, dev, g, dL, rast, n_pairs, 1)
+        result["rect_mode_2"] = run_rect_mode(args, dev, g, dL, rast, n_pairs, 2)
         result["mip"] = run_mip(args, dev, g, dL, rast)
     if args.sweep:
         result["sweep"] = run_sweep(args, dev)
@@ -712,12 +713,13 @@ def _run_variant(args, dev, g, dL, rast0, label, **cfg_kw):
     return ms, pix / (ms * 1e3), pairs, (10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf"))
 
 
-def run_rect_mode1(args, dev, g, dL, rast0, pairs0):
+def run_rect_mode(args, dev, g, dL, rast0, pairs0, mode):
     """The same step with the per-half valid regions of Sec. 3.4 as tile rectangles
-    (hgs_config.rect_mode = 1): time, pair count, and the PSNR of its image against the
-    3-sigma-square image of the main run (the two rules differ where a splat reaches
+    (hgs_config.rect_mode = 1: exact cut ellipse at the splitting plane; 2: Algorithm 1's
+    flattened covariance there): time, pair count, and the PSNR of its image against
+    the 3-sigma-square image of the main run (the rules differ where a splat reaches
     beyond its 3-sigma ellipse)."""
-    ms, mpix, pairs, psnr = _run_variant(args, dev, g, dL, rast0, "rect_mode 1", rect_mode=1)
+    ms, mpix, pairs, psnr = _run_variant(args, dev, g, dL, rast0, f"rect_mode {mode}", rect_mode=mode)
     return {"ms_per_step": ms, "Mpixel_per_s": mpix, "pairs": pairs, "pairs_rect_mode_0": pairs0,
             "psnr_vs_rect_mode_0_db": psnr}
 
@@ -981,7 +983,7 @@ def main(argv=None):
     ap.add_argument("--mv-steps", type=int, default=10)
     ap.add_argument("--sweep", action="store_true", help="also time the stress sweep (100k..6M splats)")
     ap.add_argument("--no-rect-modes", dest="rect_modes", action="store_false",
-                    help="skip the steps with per-half tile rectangles (rect_mode 1) and with the "
+                    help="skip the steps with per-half tile rectangles (rect_mode 1 and 2) and with the "
                          "Mip-Splatting 2D filter (mip)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     args = ap.parse_args(argv)

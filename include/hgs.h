@@ -123,6 +123,11 @@ typedef struct {
  *                    cut ellipse elsewhere; low-pass added in quadrature); a splat
  *                    with both halves below 1/255 is culled.  Mode 1 changes the
  *                    image where a splat reached beyond its 3-sigma ellipse.
+ *                    2 = as 1, with the splitting edge taken from Algorithm 1
+ *                    (Suppl. B.1): the projection of the flattened covariance
+ *                    whose in-plane part is the Gaussian's covariance given the
+ *                    normal coordinate and whose variance along n is a hundredth
+ *                    of the smaller in-plane one (a little wider than mode 1). 
  *   mip            : 1 = Mip-Splatting-HGS: the low-pass is Mip-Splatting's 2D
  *                    filter, a normalised convolution with N(0, lowpass I) rather
  *                    than a dilation, so both opacities are scaled by
@@ -133,7 +138,7 @@ typedef struct {
  *                    Mip-Splatting's 3D filter needs no kernel: it is the scales
  *                    sqrt(s^2 + s_f^2) and opacities scaled by prod s / prod
  *                    sqrt(s^2 + s_f^2), applied by the caller.  The rect_mode 1
- *                    opacity test uses the unscaled opacities (a superset). */
+ *                    and 2 opacity test uses the unscaled opacities (a superset). */
 typedef struct {
     int tile_w, tile_h;
     int batch;

@@ -38,9 +38,9 @@ bool cfg_ok(const hgs_config *c) {
     if (!c) return false;
     const bool shape = (c->tile_w == 16 && c->tile_h == 16) || (c->tile_w == 8 && c->tile_h == 8) ||
                        (c->tile_w == 32 && c->tile_h == 8);
-    const bool batch = c->batch == 0 || c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256 ||
-                       c->batch == 512;
-    const bool rect = c->rect_mode == 0 || c->rect_mode == 1;
+    const bool batch = c->batch == 0 || c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 224 ||
+                       c->batch == 256 || c->batch == 512;
+    const bool rect = c->rect_mode == 0 || c->rect_mode == 1 || c->rect_mode == 2;
     const bool mip = c->mip == 0 || c->mip == 1;
     return shape && batch && rect && mip && isfinite(c->lowpass) && c->lowpass >= 0.0f;
 }

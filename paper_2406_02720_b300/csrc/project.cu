@@ -252,7 +252,7 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     if (!(isfinite(mux) && isfinite(muy) && isfinite(r))) return;
     // 15. extents towards -x, +x, -y, +y: the 3-sigma radius (3D-GS), or per half
     float ex0 = r, ex1 = r, ey0 = r, ey1 = r;
-    if (rect_mode == 1) {
+    if (rect_mode == 1 || rect_mode == 2) {
         // 15a. 1-sigma support of each half under the projection, without the low-pass:
         // the whole ellipse (A0, C0) where the half's outer edge faces that way (sign of
         // k = P L^T n^), else the cut ellipse of the splitting plane (Ar, Cr)
@@ -279,9 +279,77 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
             K1 = fm(o.P[1][0], u[0]);
             K1 = fa(K1, fm(o.P[1][1], u[1]));
             K1 = fa(K1, fm(o.P[1][2], u[2]));
-            if (vs > 0.0f) {
+            if (vs > 0.0f && rect_mode == 1) {
                 Ar = fmaxf(0.0f, fs(A0, fdv(fm(K0, K0), vs)));
                 Cr = fmaxf(0.0f, fs(C0, fdv(fm(K1, K1), vs)));
+            } else if (vs > 0.0f) {
+                // 15a'. Algorithm 1 (Suppl. B.1): basis (v1, v2, n^) of the splitting plane,
+                // the covariance in it from the rows L^T v1, L^T v2, u = L^T n^, the in-plane
+                // covariance given the normal coordinate (a', b', c'), a third variance
+                // min(a', c') / 100 along n^, and the diagonal of M sigma M^T for the
+                // flattened covariance sigma in place of the cut ellipse's
+                float v1[3], v2[3];
+                if (h0 == 0.0f && h1 == 0.0f) {
+                    v1[0] = 1.0f; v1[1] = 0.0f; v1[2] = 0.0f;
+                    v2[0] = 0.0f; v2[1] = 1.0f; v2[2] = 0.0f;
+                } else {
+                    const float l1 = __fsqrt_rn(fa(fm(h1, h1), fm(h0, h0)));
+                    v1[0] = fdv(h1, l1); v1[1] = -fdv(h0, l1); v1[2] = 0.0f;
+                    const float c0 = -fm(h2, v1[1]);      // n^ x v1 with v1[2] = 0
+                    const float c1 = fm(h2, v1[0]);
+                    const float c2 = fs(fm(h0, v1[1]), fm(h1, v1[0]));
+                    float l2 = fm(c0, c0);
+                    l2 = fa(l2, fm(c1, c1));
+                    l2 = __fsqrt_rn(fa(l2, fm(c2, c2)));
+                    v2[0] = fdv(c0, l2); v2[1] = fdv(c1, l2); v2[2] = fdv(c2, l2);
+                }
+                float g1[3], g2[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float acc = fm(o.L[0][k], v1[0]);
+                    acc = fa(acc, fm(o.L[1][k], v1[1]));
+                    g1[k] = fa(acc, fm(o.L[2][k], v1[2]));
+                    acc = fm(o.L[0][k], v2[0]);
+                    acc = fa(acc, fm(o.L[1][k], v2[1]));
+                    g2[k] = fa(acc, fm(o.L[2][k], v2[2]));
+                }
+                float s00 = fm(g1[0], g1[0]), s01 = fm(g1[0], g2[0]), s11 = fm(g2[0], g2[0]);
+                float s02 = fm(g1[0], u[0]), s12 = fm(g2[0], u[0]);
+#pragma unroll
+                for (int k = 1; k < 3; ++k) {
+                    s00 = fa(s00, fm(g1[k], g1[k]));
+                    s01 = fa(s01, fm(g1[k], g2[k]));
+                    s11 = fa(s11, fm(g2[k], g2[k]));
+                    s02 = fa(s02, fm(g1[k], u[k]));
+                    s12 = fa(s12, fm(g2[k], u[k]));
+                }
+                const float ap = fs(s00, fdv(fm(s02, s02), vs));
+                const float bp = fs(s01, fdv(fm(s02, s12), vs));
+                const float cp = fs(s11, fdv(fm(s12, s12), vs));
+                const float tt = fdv(fminf(ap, cp), 100.0f);
+                float qv[2][3];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    float acc = fm(M[i][0], v1[0]);
+                    acc = fa(acc, fm(M[i][1], v1[1]));
+                    qv[i][0] = fa(acc, fm(M[i][2], v1[2]));
+                    acc = fm(M[i][0], v2[0]);
+                    acc = fa(acc, fm(M[i][1], v2[1]));
+                    qv[i][1] = fa(acc, fm(M[i][2], v2[2]));
+                    acc = fm(M[i][0], h0);
+                    acc = fa(acc, fm(M[i][1], h1));
+                    qv[i][2] = fa(acc, fm(M[i][2], h2));
+                }
+                float As = fm(ap, fm(qv[0][0], qv[0][0]));
+                As = fa(As, fm(fm(2.0f, bp), fm(qv[0][0], qv[0][1])));
+                As = fa(As, fm(cp, fm(qv[0][1], qv[0][1])));
+                As = fa(As, fm(tt, fm(qv[0][2], qv[0][2])));
+                float Cs = fm(ap, fm(qv[1][0], qv[1][0]));
+                Cs = fa(Cs, fm(fm(2.0f, bp), fm(qv[1][0], qv[1][1])));
+                Cs = fa(Cs, fm(cp, fm(qv[1][1], qv[1][1])));
+                Cs = fa(Cs, fm(tt, fm(qv[1][2], qv[1][2])));
+                Ar = fmaxf(0.0f, As);
+                Cr = fmaxf(0.0f, Cs);
             }
         }
         // 15b. a half is splatted when its opacity reaches the 1/255 floor

@@ -38,8 +38,10 @@ def test_host_validation_rejects_bad_arguments():
     assert L.hgs_layout(cams, 1, ctypes.byref(bad_tile), None, None) == H.HGS_ERR_INVALID
     bad_batch = H.make_config(batch=48)
     assert L.hgs_layout(cams, 1, ctypes.byref(bad_batch), None, None) == H.HGS_ERR_INVALID
-    bad_rect = H.make_config(rect_mode=2)
+    bad_rect = H.make_config(rect_mode=3)
     assert L.hgs_layout(cams, 1, ctypes.byref(bad_rect), None, None) == H.HGS_ERR_INVALID
+    for ok in (H.make_config(rect_mode=2), H.make_config(batch=224)):
+        assert L.hgs_layout(cams, 1, ctypes.byref(ok), None, None) == H.HGS_OK
     bad_mip = H.make_config()
     bad_mip.mip = 2
     assert L.hgs_layout(cams, 1, ctypes.byref(bad_mip), None, None) == H.HGS_ERR_INVALID

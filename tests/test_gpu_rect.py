@@ -1,6 +1,7 @@
-"""rect_mode 1 (the per-half valid region of Sec. 3.4) on the GPU against the oracle's
-same rule: bit-exact binning for every tile shape, images and gradients, and fewer
-(tile, splat) pairs than the 3-sigma square."""
+"""rect_mode 1 (the per-half valid region of Sec. 3.4) and rect_mode 2 (the same with
+the splitting edge from Algorithm 1's flattened covariance) on the GPU against the
+oracle's same rules: bit-exact binning for every tile shape, images and gradients, and
+fewer (tile, splat) pairs than the 3-sigma square."""
 import numpy as np
 import pytest
 
@@ -23,11 +24,12 @@ def _scene_with_transparent_halves(seed=33, n=2500):
     return sc, [scenes.identity_camera(160, 96, 110.0, bg=(0.1, 0.1, 0.2))]
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
-def test_rect_mode1_binning_bit_exact(cuda_ok, tile):
+def test_rect_mode_binning_bit_exact(cuda_ok, tile, mode):
     sc, cams = _scene_with_transparent_halves()
-    out = gpu_render(sc, cams, tile=tile, rect_mode=1)
-    pr = oracle.project(sc, cams[0], tile=tile, rect_mode=1)
+    out = gpu_render(sc, cams, tile=tile, rect_mode=mode)
+    pr = oracle.project(sc, cams[0], tile=tile, rect_mode=mode)
     ref = oracle.bin_pairs(pr, cams[0], tile)
     assert np.array_equal(out["rect"][0], pr["rect"])
     assert np.array_equal(out["tiles"][0], pr["tiles"])
@@ -37,23 +39,25 @@ def test_rect_mode1_binning_bit_exact(cuda_ok, tile):
     assert pr["tiles"].sum() < 0.8 * sq["tiles"].sum()
 
 
-def test_rect_mode1_image_and_gradients(cuda_ok):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_rect_mode_image_and_gradients(cuda_ok, mode):
     sc, cams = _scene_with_transparent_halves(seed=34)
-    ref = oracle.render(sc, cams[0], rect_mode=1)
+    ref = oracle.render(sc, cams[0], rect_mode=mode)
     dL = masked_upstream(scenes.upstream_grad(35, cams), [ref])
-    out = gpu_render(sc, cams, dL=dL, rect_mode=1)
-    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="rect_mode 1")
+    out = gpu_render(sc, cams, dL=dL, rect_mode=mode)
+    compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label=f"rect_mode {mode}")
     gref = oracle.render_bwd(sc, cams[0], dL[0], proj=ref["proj"], bins=ref["bins"])
     for k in ("means", "scales", "quats", "normals", "opac1", "opac2", "sh"):
-        check_grads(out["grads"][k], gref[k], ref["touched"], label=f"rect_mode 1 {k}", err=gref["err_" + k])
+        check_grads(out["grads"][k], gref[k], ref["touched"], label=f"rect_mode {mode} {k}", err=gref["err_" + k])
 
 
-def test_rect_mode1_on_the_blob_scene(cuda_ok):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_rect_mode_on_the_blob_scene(cuda_ok, mode):
     """A 200k-splat cut of the benchmark's blob scene at 1920x1080: same pairs as the
     oracle's rule, a third fewer than the 3-sigma square."""
     sc, cams = scenes.config3(n=200_000)
-    out = gpu_render(sc, cams, rect_mode=1)
-    pr = oracle.project(sc, cams[0], rect_mode=1)
+    out = gpu_render(sc, cams, rect_mode=mode)
+    pr = oracle.project(sc, cams[0], rect_mode=mode)
     ref = oracle.bin_pairs(pr, cams[0])
     assert np.array_equal(out["keys"], ref["keys"]) and np.array_equal(out["ids"], ref["ids"])
     sq = oracle.project(sc, cams[0], rect_mode=0)
