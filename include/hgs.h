@@ -192,6 +192,13 @@ size_t hgs_bin_workspace_size(int n, int n_views, size_t pair_capacity);
 size_t hgs_render_workspace_size(const hgs_camera *cams_host, int n_views, const hgs_config *cfg,
                                  int n);
 
+/* uint32 words of the visibility mask that hgs_render_fwd writes and the backward
+ * compositing reads, for up to pair_capacity (tile, splat) pairs:
+ * (pair_capacity / 32 + total_tiles + 1) * tile_w * tile_h / 32.  0 on a bad
+ * camera or option. */
+size_t hgs_vis_words(const hgs_camera *cams_host, int n_views, const hgs_config *cfg,
+                     size_t pair_capacity);
+
 /* ---- A1-A2: projection and SH colour ------------------------------------ */
 
 /* Projects every splat into every view: Sigma^w = R S S^T R^T (Eq. 2),
@@ -258,12 +265,24 @@ hgs_status hgs_bin_static(const hgs_proj *proj, int n, const hgs_camera *cams_ho
  *   image     [3*total_pixels] : C + T_final * bg, per view [3,H,W]
  *   final_T   [total_pixels]   : T after the last composited splat
  *   n_contrib [total_pixels]   : 1 + position (in the tile's list) of the last
- *                                composited splat, 0 if none               */
+ *                                composited splat, 0 if none
+ *   vis       [vis_words]      : visibility mask, hgs_vis_words() words for the
+ *                                pair capacity.  Per tile t with sorted list
+ *                                [beg, end), per 32-entry chunk c of that list
+ *                                and per 8x4 pixel block w of the tile (row-major
+ *                                blocks), the word at
+ *                                ((beg >> 5) + t + c) * (tile_w*tile_h/32) + w
+ *                                has bit j set iff entry beg + 32c + j was
+ *                                composited at some pixel of block w.  Words of
+ *                                chunks past every pixel's last composited entry
+ *                                are left as they were.  A word beyond vis_words
+ *                                is not written and sets HGS_DEV_CAPACITY.     */
 hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
                           const uint32_t *ranges, const hgs_camera *cams_host,
                           const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                           void *ws, size_t ws_bytes, float *image, float *final_T,
-                          uint32_t *n_contrib, int *dev_status, void *stream);
+                          uint32_t *n_contrib, uint32_t *vis, size_t vis_words,
+                          int *dev_status, void *stream);
 
 /* ---- A7: backward compositing ---------------------------------------------- */
 
@@ -275,14 +294,19 @@ hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
  *          d w'_x, d w'_y, d alpha1, d alpha2, d r, d g, d b.
  * The call zeroes grad2d first.  Gradients through the 0.99 clamp, through
  * skipped or terminated splats and through P of a degenerate plane are 0.
+ * final_T, n_contrib and vis are the outputs of the hgs_render_fwd being
+ * differentiated (same inputs, tile shape and batch): each 8x4 pixel block visits
+ * only the entries its vis words mark, and every pixel re-evaluates those with
+ * the forward's arithmetic, so its decisions are the forward's.  A word beyond
+ * vis_words counts as all ones (every entry visited; same result, slower).
  * Within a block, one warp stages each tile's list in batches and the others walk
  * them, synchronised by bounded waits: HGS_DEV_TIMEOUT if one runs out. */
 hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids,
                              const uint32_t *ranges, const hgs_camera *cams_host,
                              const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                              void *ws, size_t ws_bytes, const float *final_T,
-                             const uint32_t *n_contrib, const float *dL_dimage,
-                             float *grad2d, int *dev_status, void *stream);
+                             const uint32_t *n_contrib, const uint32_t *vis, size_t vis_words,
+                             const float *dL_dimage, float *grad2d, int *dev_status, void *stream);
 
 /* ---- A8: projection backward ------------------------------------------------ */
 
@@ -301,7 +325,8 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
                           const uint32_t *ranges, const hgs_camera *cams_host,
                           const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                           void *ws, size_t ws_bytes, const float *final_T,
-                          const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                          const uint32_t *n_contrib, const uint32_t *vis, size_t vis_words,
+                          const float *dL_dimage, float *grad2d,
                           const hgs_gaussian_grads *out, int *dev_status, void *stream);
 
 /* ---- measurement ------------------------------------------------------------------- */
@@ -317,8 +342,8 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
 hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                             const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                             const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
-                            uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
-                            unsigned long long *counters, int *dev_status, void *stream);
+                            uint32_t *n_contrib, uint32_t *vis, size_t vis_words, const float *dL_dimage,
+                            float *grad2d, unsigned long long *counters, int *dev_status, void *stream);
 
 /* Issue-rate probe for the compositing kernels' roofline (the paper has no
  * counterpart: it measures this GPU, not the method).  kind 0 runs independent

@@ -61,7 +61,7 @@ def lib():
         L.or_render_fwd.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, POINTER(c_uint32),
                                     POINTER(c_uint32), POINTER(OrCamera), POINTER(OrOpts),
                                     POINTER(c_ubyte), dp, dp, ip, dp, dp, dp, ip,
-                                    dp, dp, dp, dp, POINTER(c_ubyte)]
+                                    dp, dp, dp, dp, POINTER(c_ubyte), POINTER(c_ubyte)]
         L.or_error_basis.argtypes = [c_int, dp, dp, dp, dp, POINTER(OrCamera), POINTER(OrOpts), ip,
                                      POINTER(c_ubyte), dp, dp]
         L.or_pair_bands.argtypes = [c_int, ip, dp, dp, dp, dp, dp, dp, c_int, c_int, c_int, ip, dp, dp, dp, dp]
@@ -242,7 +242,7 @@ def bin_pairs(proj, cam, tile=(16, 16), tile_mask=None):
 
 
 def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, tile_mask=None,
-           proj=None, bins=None, rect_mode=0, mip=False, margins=True):
+           proj=None, bins=None, rect_mode=0, mip=False, margins=True, composited=False):
     """Forward image: front-to-back compositing of the Eq. 10 pair weights over each
     tile's depth-sorted list (3-sigma tile culling, 1/255 floor, 0.99 clamp, 1e-4 stop).
 
@@ -254,7 +254,10 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     there (<= 1: FP32 cannot be expected to decide it as FP64 does); flip_img, flip_T:
     how far those decisions can move the pixel; touched [N]: splats with such a
     decision in some pixel.  margins=False skips the error model (its outputs are then
-    absent): the render alone, as the CPU baseline times it."""
+    absent): the render alone, as the CPU baseline times it.  composited=True adds
+    comp [pairs, tile_h, tile_w] (bool): entry j of the sorted pair list is composited
+    at that pixel of its tile (Sec. 3.3 blending: before the stop, at or above the
+    1/255 floor)."""
     if proj is None:
         proj = project(sc, cam, tile, lowpass, fov_clamp, rect_mode, mip, errmat=margins)
     if bins is None:
@@ -286,6 +289,7 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
     if ids.size == 0:
         ids = np.zeros(1, np.uint32)
     dp = c_double
+    comp = np.zeros((max(int(bins["ids"].size), 1), tile[1], tile[0]), np.uint8) if composited else None
     lib().or_render_fwd(proj["mode"].shape[0], _p(proj["mode"], c_int), _p(proj["mu2"], dp),
                         _p(proj["conic"], dp), _p(proj["wp"], dp), _p(proj["rgb"], dp),
                         _p(proj["opac1"], dp), _p(proj["opac2"], dp), _p(ids, c_uint32),
@@ -293,12 +297,14 @@ def render(sc, cam, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True, til
                         _p(image, dp), _p(T, dp), _p(nc, c_int), _p(mg, dp),
                         _p(mga, dp) if margins else None, _p(mgT, dp) if margins else None,
                         _p(ncomp, c_int), em_p, *((_p(mgc, dp), _p(flip_img, dp), _p(flip_T, dp), _p(touched, c_ubyte))
-                                                  if margins else (None, None, None, None)))
+                                                  if margins else (None, None, None, None)),
+                        _p(comp, c_ubyte) if composited else None)
+    extra = dict(comp=comp[:int(bins["ids"].size)].astype(bool)) if composited else {}
     if not margins:
-        return dict(image=image, T=T, n_contrib=nc, n_comp=ncomp, proj=proj, bins=bins)
+        return dict(image=image, T=T, n_contrib=nc, n_comp=ncomp, proj=proj, bins=bins, **extra)
     return dict(image=image, T=T, n_contrib=nc, margin=mg, margin_a=mga, margin_T=mgT, margin_c=mgc,
                 n_comp=ncomp, flip_img=flip_img, flip_T=flip_T, touched=touched.astype(bool),
-                proj=proj, bins=bins)
+                proj=proj, bins=bins, **extra)
 
 
 def rasterize_bwd(sc, cam, dL_dimage, tile=(16, 16), lowpass=0.3, plain=False, fov_clamp=True,

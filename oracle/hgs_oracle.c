@@ -64,7 +64,7 @@ enum { OR_CULLED = 0, OR_NORMAL = 1, OR_STEP = 2, OR_HALF = 3 };
 #define OR_ALPHA_MAX 0.99
 #define OR_T_MIN 1e-4
 
-int or_abi_version(void) { return 7; }
+int or_abi_version(void) { return 8; }
 
 /* Algorithm 1 (Suppl. B.1), step by step in binary64: the covariance `out` (3x3,
  * row-major) of the flattened ellipsoid that holds the cut of the Gaussian of
@@ -1042,8 +1042,10 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
                   double *image, double *T_out, int *n_contrib, double *margin,
                   double *margin_a, double *margin_T, int *n_comp,
                   const double *errmat, double *margin_c, double *flip_img, double *flip_T,
-                  unsigned char *touched)
+                  unsigned char *touched, unsigned char *comp)
 {
+    /* comp (optional, [pairs, tile_w * tile_h], zeroed by the caller): comp[j, q] = 1
+     * where list entry j is composited at pixel q (row-major within its tile).      */
     (void)n;
     splats2d_t s = {mode, mu2, conic, wp, rgb, op1, op2};
     int W = cam->width, H = cam->height;
@@ -1123,6 +1125,9 @@ int or_render_fwd(int n, const int *mode, const double *mu2, const double *conic
                         if (touched) touched[i] = 1;
                     }
                     if (Tn < OR_T_MIN) break;
+                    if (comp)
+                        comp[(size_t)j * (o->tile_w * o->tile_h) + (py - ty * o->tile_h) * o->tile_w +
+                             (px - tx * o->tile_w)] = 1;
                     for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * e.a * T;
                     T = Tn;
                     t_err += this_err;

@@ -128,6 +128,12 @@ size_t hgs_render_workspace_size(const hgs_camera *cams_host, int n_views, const
     return render_workspace_bytes(vt, *cfg);
 }
 
+size_t hgs_vis_words(const hgs_camera *cams_host, int n_views, const hgs_config *cfg, size_t pair_capacity) {
+    ViewTable vt;
+    if (build_views(cams_host, n_views, cfg, &vt) != HGS_OK || pair_capacity > HGS_MAX_PAIRS) return 0;
+    return vis_words_for(pair_capacity, vt.total_tiles, cfg->tile_w, cfg->tile_h);
+}
+
 hgs_status hgs_project(const hgs_gaussians *g, const hgs_camera *cams_host, const hgs_camera *cams_dev,
                        int n_views, const hgs_config *cfg, const hgs_proj *out, int *dev_status, void *stream) {
     ViewTable vt;
@@ -197,6 +203,8 @@ static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids
     p->image = nullptr;
     p->final_T = nullptr;
     p->n_contrib = nullptr;
+    p->vis = nullptr;
+    p->vis_words = 0;
     p->dL_dimage = nullptr;
     p->grad2d = nullptr;
     p->status = nullptr;
@@ -207,14 +215,16 @@ static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids
 hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                           const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                           const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
-                          uint32_t *n_contrib, int *dev_status, void *stream) {
+                          uint32_t *n_contrib, uint32_t *vis, size_t vis_words, int *dev_status, void *stream) {
     RenderLaunch p;
     hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
     if (st != HGS_OK) return st;
-    if (!image || !final_T || !n_contrib) return HGS_ERR_INVALID;
+    if (!image || !final_T || !n_contrib || !vis) return HGS_ERR_INVALID;
     p.image = image;
     p.final_T = final_T;
     p.n_contrib = n_contrib;
+    p.vis = vis;
+    p.vis_words = vis_words;
     p.status = dev_status;
     return cuda_status(launch_render_fwd(p, static_cast<cudaStream_t>(stream)));
 }
@@ -222,14 +232,17 @@ hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids, cons
 hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                              const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                              const hgs_config *cfg, void *ws, size_t ws_bytes, const float *final_T,
-                             const uint32_t *n_contrib, const float *dL_dimage, float *grad2d, int *dev_status,
-                             void *stream) {
+                             const uint32_t *n_contrib, const uint32_t *vis, size_t vis_words,
+                             const float *dL_dimage, float *grad2d, int *dev_status, void *stream) {
     RenderLaunch p;
     hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
     if (st != HGS_OK) return st;
-    if (!final_T || !n_contrib || !dL_dimage || (n > 0 && (!grad2d || !aligned16(grad2d)))) return HGS_ERR_INVALID;
+    if (!final_T || !n_contrib || !vis || !dL_dimage || (n > 0 && (!grad2d || !aligned16(grad2d))))
+        return HGS_ERR_INVALID;
     p.final_T = const_cast<float *>(final_T);
     p.n_contrib = const_cast<uint32_t *>(n_contrib);
+    p.vis = const_cast<uint32_t *>(vis);
+    p.vis_words = vis_words;
     p.dL_dimage = dL_dimage;
     p.grad2d = grad2d;
     p.status = dev_status;
@@ -239,16 +252,19 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, c
 hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                             const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                             const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
-                            uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
-                            unsigned long long *counters, int *dev_status, void *stream) {
+                            uint32_t *n_contrib, uint32_t *vis, size_t vis_words, const float *dL_dimage,
+                            float *grad2d, unsigned long long *counters, int *dev_status, void *stream) {
     RenderLaunch p;
     hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
     if (st != HGS_OK) return st;
-    if (!image || !final_T || !n_contrib || !dL_dimage || !counters || (n > 0 && (!grad2d || !aligned16(grad2d))))
+    if (!image || !final_T || !n_contrib || !vis || !dL_dimage || !counters ||
+        (n > 0 && (!grad2d || !aligned16(grad2d))))
         return HGS_ERR_INVALID;
     p.image = image;
     p.final_T = final_T;
     p.n_contrib = n_contrib;
+    p.vis = vis;
+    p.vis_words = vis_words;
     p.dL_dimage = dL_dimage;
     p.grad2d = grad2d;
     p.status = dev_status;
@@ -286,11 +302,11 @@ hgs_status hgs_project_bwd(const hgs_gaussians *g, const hgs_camera *cams_host, 
 hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const uint32_t *ids, const uint32_t *ranges,
                           const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                           void *ws, size_t ws_bytes, const float *final_T, const uint32_t *n_contrib,
-                          const float *dL_dimage, float *grad2d, const hgs_gaussian_grads *out, int *dev_status,
-                          void *stream) {
+                          const uint32_t *vis, size_t vis_words, const float *dL_dimage, float *grad2d,
+                          const hgs_gaussian_grads *out, int *dev_status, void *stream) {
     if (!g) return HGS_ERR_INVALID;
     hgs_status st = hgs_rasterize_bwd(proj, g->n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes,
-                                      final_T, n_contrib, dL_dimage, grad2d, dev_status, stream);
+                                      final_T, n_contrib, vis, vis_words, dL_dimage, grad2d, dev_status, stream);
     if (st != HGS_OK) return st;
     return hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, proj->fp64_list, dev_status, stream);
 }

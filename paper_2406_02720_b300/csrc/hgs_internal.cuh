@@ -78,6 +78,19 @@ struct BinLaunch {
 size_t bin_workspace_bytes(int n, int n_views, size_t capacity);
 cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s);
 
+// Visibility mask, written by the forward compositing and read by the backward.  For
+// each global tile t (sorted list [beg_t, end_t)) and each 32-entry chunk c of that list
+// there is one 32-bit word per 8x4 warp block w of the tile, at
+//   (vis_row(beg_t, t) + c) * (warps per tile) + w;
+// bit j says that list entry beg_t + 32c + j was composited at some pixel of block w.
+// Tile t's rows never reach tile t+1's: ceil(len/32) <= (end >> 5) - (beg >> 5) + 1.
+__host__ __device__ __forceinline__ size_t vis_row(uint32_t beg, int gtile) {
+    return (size_t)(beg >> 5) + (size_t)gtile;
+}
+inline size_t vis_words_for(size_t pair_capacity, int total_tiles, int tile_w, int tile_h) {
+    return (pair_capacity / 32 + (size_t)total_tiles + 1) * (size_t)(tile_w * tile_h / 32);
+}
+
 struct RenderLaunch {
     hgs_proj proj;
     int n;
@@ -92,6 +105,8 @@ struct RenderLaunch {
     float *image;
     float *final_T;
     uint32_t *n_contrib;
+    uint32_t *vis;                  // visibility mask (forward output, backward input)
+    size_t vis_words;
     // backward
     const float *dL_dimage;
     float *grad2d;

@@ -78,6 +78,8 @@ def lib():
         L.hgs_bin_workspace_size.argtypes = [c_int, c_int, c_size_t]
         L.hgs_render_workspace_size.restype = c_size_t
         L.hgs_render_workspace_size.argtypes = [_CAM_P, c_int, _CFG_P, c_int]
+        L.hgs_vis_words.restype = c_size_t
+        L.hgs_vis_words.argtypes = [_CAM_P, c_int, _CFG_P, c_size_t]
         L.hgs_project.restype = c_int
         L.hgs_project.argtypes = [POINTER(HgsGaussians), _CAM_P, vp, c_int, _CFG_P, POINTER(HgsProj), vp, vp]
         L.hgs_bin.restype = c_int
@@ -88,19 +90,20 @@ def lib():
                                      vp]
         L.hgs_render_fwd.restype = c_int
         L.hgs_render_fwd.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp,
-                                     c_size_t, vp, vp, vp, vp, vp]
+                                     c_size_t, vp, vp, vp, vp, c_size_t, vp, vp]
         L.hgs_rasterize_bwd.restype = c_int
         L.hgs_rasterize_bwd.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp,
-                                        c_size_t, vp, vp, vp, vp, vp, vp]
+                                        c_size_t, vp, vp, vp, c_size_t, vp, vp, vp, vp]
         L.hgs_project_bwd.restype = c_int
         L.hgs_project_bwd.argtypes = [POINTER(HgsGaussians), _CAM_P, vp, c_int, _CFG_P, vp,
                                       POINTER(HgsGaussianGrads), vp, vp, vp]
         L.hgs_render_stats.restype = c_int
         L.hgs_render_stats.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp, c_size_t,
-                                       vp, vp, vp, vp, vp, vp, vp, vp]
+                                       vp, vp, vp, vp, c_size_t, vp, vp, vp, vp, vp]
         L.hgs_render_bwd.restype = c_int
         L.hgs_render_bwd.argtypes = [POINTER(HgsGaussians), POINTER(HgsProj), vp, vp, _CAM_P, vp, c_int,
-                                     _CFG_P, vp, c_size_t, vp, vp, vp, vp, POINTER(HgsGaussianGrads), vp, vp]
+                                     _CFG_P, vp, c_size_t, vp, vp, vp, c_size_t, vp, vp,
+                                     POINTER(HgsGaussianGrads), vp, vp]
         L.hgs_probe_peak.restype = c_int
         L.hgs_probe_peak.argtypes = [c_int, c_int, c_int, vp, POINTER(ctypes.c_double), vp]
         L.hgs_selftest_wait.restype = c_int
@@ -147,6 +150,10 @@ def hgs_render_workspace_size(cams_host, n_views, cfg, n) -> int:
     return int(lib().hgs_render_workspace_size(cams_host, n_views, ctypes.byref(cfg), n))
 
 
+def hgs_vis_words(cams_host, n_views, cfg, pair_capacity) -> int:
+    return int(lib().hgs_vis_words(cams_host, n_views, ctypes.byref(cfg), pair_capacity))
+
+
 def hgs_project(g, cams_host, cams_dev, n_views, cfg, out, dev_status, stream):
     _check(lib().hgs_project(ctypes.byref(g), cams_host, cams_dev, n_views, ctypes.byref(cfg),
                              ctypes.byref(out), dev_status, stream), "hgs_project")
@@ -170,17 +177,17 @@ def hgs_bin_static(proj, n, cams_host, n_views, cfg, pair_capacity, keys_out, id
 
 
 def hgs_render_fwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, image, final_T,
-                   n_contrib, dev_status, stream):
+                   n_contrib, vis, vis_words, dev_status, stream):
     _check(lib().hgs_render_fwd(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
-                                ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, dev_status, stream),
-           "hgs_render_fwd")
+                                ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, vis, vis_words,
+                                dev_status, stream), "hgs_render_fwd")
 
 
 def hgs_rasterize_bwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, final_T,
-                      n_contrib, dL_dimage, grad2d, dev_status, stream):
+                      n_contrib, vis, vis_words, dL_dimage, grad2d, dev_status, stream):
     _check(lib().hgs_rasterize_bwd(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
-                                   ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, dL_dimage, grad2d,
-                                   dev_status, stream), "hgs_rasterize_bwd")
+                                   ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, vis, vis_words, dL_dimage,
+                                   grad2d, dev_status, stream), "hgs_rasterize_bwd")
 
 
 def hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, fp64_list, dev_status, stream):
@@ -189,17 +196,17 @@ def hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, fp64_list
 
 
 def hgs_render_bwd(g, proj, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, final_T, n_contrib,
-                   dL_dimage, grad2d, out, dev_status, stream):
+                   vis, vis_words, dL_dimage, grad2d, out, dev_status, stream):
     _check(lib().hgs_render_bwd(ctypes.byref(g), ctypes.byref(proj), ids, ranges, cams_host, cams_dev, n_views,
-                                ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, dL_dimage, grad2d,
-                                ctypes.byref(out), dev_status, stream), "hgs_render_bwd")
+                                ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, vis, vis_words, dL_dimage,
+                                grad2d, ctypes.byref(out), dev_status, stream), "hgs_render_bwd")
 
 
 def hgs_render_stats(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, image, final_T,
-                     n_contrib, dL_dimage, grad2d, counters, dev_status, stream):
+                     n_contrib, vis, vis_words, dL_dimage, grad2d, counters, dev_status, stream):
     _check(lib().hgs_render_stats(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
-                                  ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, dL_dimage, grad2d,
-                                  counters, dev_status, stream), "hgs_render_stats")
+                                  ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, vis, vis_words,
+                                  dL_dimage, grad2d, counters, dev_status, stream), "hgs_render_stats")
 
 
 def hgs_probe_peak(kind, blocks_per_sm, iters, sink, stream) -> float:

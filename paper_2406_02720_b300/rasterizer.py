@@ -111,6 +111,9 @@ class Rasterizer:
         self.ids = torch.empty(cap, dtype=torch.int32, device=self.device)
         wsb = H.hgs_bin_workspace_size(self.n, self.n_views, cap)
         self.bin_ws = torch.empty(wsb, dtype=torch.uint8, device=self.device)
+        # visibility mask: written by the forward compositing, read by the backward
+        self.vis = torch.empty(H.hgs_vis_words(self.cams_host, self.n_views, self.cfg, cap), dtype=torch.int32,
+                               device=self.device)
 
     def proj_struct(self) -> H.HgsProj:
         p = H.HgsProj()
@@ -134,13 +137,14 @@ class Rasterizer:
     def render_fwd(self):
         H.hgs_render_fwd(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                          _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
-                         _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.status), self._stream())
+                         _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
+                         _vp(self.status), self._stream())
 
     def rasterize_bwd(self, dL_dimage: torch.Tensor):
         H.hgs_rasterize_bwd(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                             _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws),
-                            self.render_ws.numel(), _vp(self.final_T), _vp(self.n_contrib), _vp(dL_dimage),
-                            _vp(self.grad2d), _vp(self.status), self._stream())
+                            self.render_ws.numel(), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis),
+                            self.vis.numel(), _vp(dL_dimage), _vp(self.grad2d), _vp(self.status), self._stream())
 
     def project_bwd(self, g: Gaussians, out: Gaussians):
         H.hgs_project_bwd(g.c_struct(), self.cams_host, _vp(self.cams_dev), self.n_views, self.cfg,
@@ -163,8 +167,8 @@ class Rasterizer:
         cnt = torch.zeros(8, dtype=torch.int64, device=self.device)
         H.hgs_render_stats(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                            _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
-                           _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(dL_dimage),
-                           _vp(self.grad2d), _vp(cnt), _vp(self.status), self._stream())
+                           _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
+                           _vp(dL_dimage), _vp(self.grad2d), _vp(cnt), _vp(self.status), self._stream())
         self._raise_status(self.read_status())
         v = cnt.cpu().tolist()
         return {k: int(v[i]) for i, k in enumerate(H.STAT_NAMES)}

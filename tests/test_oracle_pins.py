@@ -378,10 +378,10 @@ def test_stacked_splats_stop_rule_and_depth_order():
     sc = Sc(means, [[sigma] * 3] * 5, [[1, 0, 0, 0]] * 5, [[0, 0, 1]] * 5, alphas, alphas,
             dc.reshape(5, 1, 3), 0)
     vm = np.zeros((3, 4)); vm[:, :3] = np.eye(3)
-    out = oracle.render(sc, Cam(vm, f, W, W), lowpass=0.0)
+    out = oracle.render(sc, Cam(vm, f, W, W), lowpass=0.0, composited=True)
     px = py = W // 2                                # centre (8.5, 8.5): d = (0.5, 0.5)
     order = np.argsort(depths)
-    T, C, last = 1.0, np.zeros(3), 0
+    T, C, last, comp = 1.0, np.zeros(3), 0, []
     for pos, i in enumerate(order):
         z = depths[i]
         G = math.exp(-(0.5 ** 2 + 0.5 ** 2) * z * z / (2 * f * f * sigma * sigma))
@@ -393,7 +393,36 @@ def test_stacked_splats_stop_rule_and_depth_order():
         C += np.asarray(cols[i]) * a * T
         T *= 1 - a
         last = pos + 1
+        comp.append(pos)
     assert last == 3            # the 4th (depth 5, opaque) stops the list; depth 6 is never reached
+    assert np.flatnonzero(out["comp"][:, py, px]).tolist() == comp == [0, 1, 2]
     np.testing.assert_allclose(out["image"][:, py, px], C, atol=1e-13)
     assert out["T"][py, px] == pytest.approx(T, rel=1e-13)
     assert out["n_contrib"][py, px] == last
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_composited_pairs_agree_with_counts(tile):
+    """The per-(pair, pixel) composited flags: in every pixel, as many entries of its
+    tile's list as the splats composited there, the last one at n_contrib - 1, and
+    none in a pixel outside the image (ragged last tiles)."""
+    rng = np.random.default_rng(41)
+    sc = scenes.scene_uniform(rng, 700, [-1.5, -1.0, 2.5], [1.5, 1.0, 6.0], -3.0, 0.6, 1.5, 1)
+    cam = scenes.identity_camera(90, 70, 60.0, 45.0, 35.0)
+    out = oracle.render(sc, cam, tile=tile, composited=True, margins=False)
+    comp, rng_t = out["comp"], out["bins"]["ranges"].reshape(-1, 2)
+    tw, th = tile
+    tiles_x = (cam.width + tw - 1) // tw
+    assert comp.any()
+    for t, (beg, end) in enumerate(rng_t):
+        tx, ty = t % tiles_x, t // tiles_x
+        for ly in range(th):
+            for lx in range(tw):
+                px, py = tx * tw + lx, ty * th + ly
+                col = comp[beg:end, ly, lx]
+                if px >= cam.width or py >= cam.height:
+                    assert not col.any()
+                    continue
+                pos = np.flatnonzero(col)
+                assert pos.size == out["n_comp"][py, px]
+                assert (pos[-1] + 1 if pos.size else 0) == out["n_contrib"][py, px]
