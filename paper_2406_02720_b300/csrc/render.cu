@@ -1,15 +1,17 @@
 // Per-pixel compositing of half-Gaussian splats (A6) and its adjoint (A7).
 //
-// Blocks walk a tile's depth-sorted list in batches that they stage in shared
-// memory (the forward uses two 128-thread blocks per 16x16 tile, one per 16x8
-// half; the backward one block of 256 pixel threads and a staging warp).  For each
-// (pixel, splat) pair:
+// A block has one thread per pixel of a tile (256 for 16x16) and one staging warp,
+// which stages the tile's depth-sorted list in batches into a ring of shared-memory
+// buffers that the pixel warps walk at their own pace, with no block barriers
+// (mbarriers with bounded waits).  For each (pixel, splat) pair:
 //   d = p - mu-hat,  hat G = exp(-1/2 |U d|^2), conic = U^T U  (Eq. 4-5)
 //   P = 1/2 erfc(-w'.d)                                         (Eq. 7-8)
 //   a = min(0.99, (alpha2 + (alpha1 - alpha2) P) hat G)          (Eq. 10)
 // composited front to back (Sec. 3.3).  A splat with a < 1/255 is skipped, and
 // a splat that would take T below 1e-4 ends the pixel's list (3D-GS rules).
-// A block stops once every pixel in it has finished (__syncthreads_count).
+// The forward's staging warp stops staging a tile once every pixel of it has finished
+// (forward 0.690 -> 0.679 ms against two 128-thread blocks per tile, each staging the
+// whole list and meeting at two block barriers per batch).
 //
 // erfc comes from Abramowitz & Stegun, Handbook of Mathematical Functions, 7.1.26
 // (|error| <= 1.5e-7 on erf), which needs exp(-z^2); the backward reuses that
@@ -41,7 +43,7 @@
 // three batch buffers and each pixel warp walks them at its own pace (mbarriers,
 // bounded waits; 1.318 -> 1.294 ms against block-synchronous batches).
 // The 12 screen-space gradients of a (warp, splat) leave as per-lane float4
-// atomic adds, with one shuffle level folding lane pairs first when more than 16
+// atomic adds, with one shuffle level folding lane pairs first when more than 12
 // lanes contribute.
 //
 // Persistent mode (the default): a grid of resident blocks pops tiles from an
@@ -306,124 +308,6 @@ struct Queue {
     uint32_t bucket_count[33];
     uint32_t bucket_cursor[33];
 };
-
-// ---- forward -------------------------------------------------------------------------
-// Pixel of a thread: warp w covers the 8x4 block (w % (TW/8), w / (TW/8)) of the tile.
-// With SPLIT blocks per tile, block `part` covers rows [part, part + 1) * TH / SPLIT.
-template <int TW>
-__device__ __forceinline__ void warp_block(const TileInfo &ti, int TH_, int row0, int &bx, int &by) {
-    const int warp = threadIdx.x >> 5;
-    bx = ti.tx * TW + (warp % (TW / 8)) * 8;
-    by = ti.ty * TH_ + row0 + (warp / (TW / 8)) * 4;
-}
-
-// Blocks per tile: each stages the tile's whole list for its own rows.  Fewer warps
-// per block wait for one another at the batch barriers, at the price of staging each
-// list once per block.  Measured at 3M splats, 1080p, 16x16 tiles: forward 0.675 ms
-// with 2 blocks per tile vs 0.683 with 1; backward 1.411 ms with 1 vs 1.447 with 2 (an
-// earlier version of the kernel).
-template <bool FWD, int TW, int TH>
-constexpr int kSplit = (FWD && TW * TH >= 256) ? 2 : 1;
-
-template <int TW, int TH, int BATCH, bool COUNT>
-__device__ __forceinline__ void render_tile_fwd(const RenderLaunch &p, int gtile, int part, Batch<BATCH, false> &s) {
-    constexpr int SPLIT = kSplit<true, TW, TH>;
-    constexpr int NT = TW * TH / SPLIT;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const TileInfo ti = tile_info<TW, TH>(p, gtile);
-    int bx, by;
-    warp_block<TW>(ti, TH, part * (TH / SPLIT), bx, by);
-    const int half = lane >> 4;             // 4x4 half of the warp's 8x4 block
-    const int px = bx + 4 * half + (lane & 3), py = by + ((lane >> 2) & 3);
-    const bool inside = px < ti.W && py < ti.H;
-    // tile-local coordinates (pixel centres at i + 1/2)
-    const int ox = ti.tx * TW, oy = ti.ty * TH;
-    const float fox = (float)ox, foy = (float)oy;
-    const f32x2 fp = pack2((float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f);
-    const float cxb = (float)(bx - ox) + 2.0f, cyb = (float)(by - oy) + 2.0f;   // left half's centre
-    const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
-    const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
-    const bool plain = p.cfg.plain != 0;
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0;
-    bool done = !inside;
-    unsigned long long c_visit = 0, c_full = 0, c_comp = 0;
-    // this warp's words of the visibility mask, one per 32 entries of the tile's list,
-    // TW*TH/32 words apart (the tile's rows are written whole or not at all)
-    constexpr int NW = TW * TH / 32;
-    const size_t vrow = vis_row(ti.beg, gtile);
-    const bool vfit = (vrow + ((ti.end - ti.beg + 31) >> 5)) * NW <= p.vis_words;
-    if (!vfit && tid == 0) set_status(p.status, HGS_DEV_CAPACITY);
-    uint32_t *vw = p.vis + (vfit ? vrow * NW + part * (NT / 32) + (tid >> 5) : 0);
-    for (uint32_t base = ti.beg; base < ti.end; base += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
-        for (int k = tid; k < BATCH; k += NT) {
-            const uint32_t j = base + k;
-            if (j < ti.end) {
-                uint32_t id = p.ids[j];
-                if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                stage<BATCH, false>(rec, id, s, k, fox, foy, plain);
-            }
-        }
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)BATCH, ti.end - base);
-        bool wdone = __all_sync(0xffffffffu, done);
-        for (int c = 0; c < cnt && !wdone; c += 32) {
-            const int jl = c + lane;
-            bool h0 = false, h1 = false;
-            if (jl < cnt) cull_halves(s, jl, cxb, cyb, h0, h1);
-            const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
-            // each half walks its own hits, the two in step
-            unsigned m = half ? m1 : m0;
-            uint32_t cm = 0;                 // chunk slots this lane composited
-            while (m) {
-                const unsigned lb = m & (0u - m);     // the visited slot's bit
-                const int k = c + __ffs(m) - 1;
-                m ^= lb;
-                if (!done) {
-                    Eval ev;
-                    if (COUNT) ++c_visit;
-                    const bool hit = eval_alpha(fp, s, k, ev);
-                    if (COUNT && ev.G >= 0.0f) ++c_full;
-                    if (hit) {
-                        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
-                        if (Tn < kTMin) {
-                            done = true;
-                        } else {
-                            if (COUNT) ++c_comp;
-                            const float w = __fmul_rn(ev.a, T);
-                            const float2 rg = *reinterpret_cast<const float2 *>(&s.g2[k].z);
-                            C0 = __fmaf_rn(rg.x, w, C0);
-                            C1 = __fmaf_rn(rg.y, w, C1);
-                            C2 = __fmaf_rn(s.b[k], w, C2);
-                            T = Tn;
-                            last = base - ti.beg + k + 1;
-                            cm |= lb;
-                        }
-                    }
-                }
-            }
-            // the chunk's mask word: splats composited at any pixel of the warp's block
-            cm = __reduce_or_sync(0xffffffffu, cm);
-            if (lane == 0 && vfit) *vw = cm;
-            vw += NW;
-            // checked once per chunk, not per visit: a warp whose lanes are all done only
-            // runs the rest of this chunk's (cheap) bit loop (render_fwd 0.711 -> 0.679 ms)
-            wdone = __all_sync(0xffffffffu, done);
-        }
-    }
-    if (inside) {
-        const size_t HW = (size_t)ti.W * ti.H;
-        const size_t pix = (size_t)py * ti.W + px;
-        float *img = p.image + 3 * (size_t)ti.pix_off;
-        img[pix] = C0 + T * ti.bg[0];
-        img[HW + pix] = C1 + T * ti.bg[1];
-        img[2 * HW + pix] = C2 + T * ti.bg[2];
-        p.final_T[ti.pix_off + pix] = T;
-        p.n_contrib[ti.pix_off + pix] = last;
-    }
-    if (COUNT) add_counters(p.counters, c_visit, c_full, c_comp, 0ull);
-}
 
 // ---- backward ------------------------------------------------------------------------
 
@@ -724,33 +608,240 @@ __device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
     if (COUNT) add_counters(p.counters + 3, c_visit, c_full, c_contrib, c_red);
 }
 
+// ---- forward -------------------------------------------------------------------------
+// The forward runs as the same kind of pipeline as the backward (below): one producer
+// warp takes tiles from the queue and stages each tile's list front to back into a ring
+// of kFwdStages batch buffers, and the TW*TH/32 consumer warps (one 8x4 pixel block each)
+// walk the batches at their own pace, with no block barriers.  A warp whose pixels have
+// all finished writes its outputs and marks the tile done; the producer stops staging a
+// tile once every consumer warp has marked it.  A tile's list is staged once per tile
+// (the earlier design staged it once per 16x8 half, in two 128-thread blocks that met at
+// two block barriers per batch).
+constexpr int kFwdStages = 3;
+
+struct FwdHeader {
+    int gtile;                  // < 0: no more work
+    uint32_t bstart, bend;      // the batch's slice of the tile's list
+    uint32_t tseq;              // 1 + the number of tiles the producer began before this one
+    int first, last;            // first / last batch of the tile's list
+};
+
+template <int BATCH, int NW>
+struct FwdRing {
+    Batch<BATCH, false> buf[kFwdStages];
+    FwdHeader hdr[kFwdStages];
+    unsigned long long full[kFwdStages], empty[kFwdStages];   // mbarriers
+    uint32_t done[NW];          // per consumer warp: tseq of the last tile it finished
+};
+
+template <int TW, int TH, int BATCH>
+__device__ void fwd_produce(const RenderLaunch &p, FwdRing<BATCH, TW * TH / 32> &r) {
+    constexpr int NB = kFwdStages, NW = TW * TH / 32;
+    const int lane = threadIdx.x & 31;
+    const float4 *rec = reinterpret_cast<const float4 *>(p.proj.rec);
+    const uint32_t vn = (uint32_t)p.n * (uint32_t)p.vt.n_views;
+    const bool plain = p.cfg.plain != 0;
+    Queue *qw = reinterpret_cast<Queue *>(p.ws);
+    const uint32_t *order = reinterpret_cast<const uint32_t *>(qw + 1);
+    uint32_t seq = 0, tseq = 0;
+    for (int round = 0;; ++round) {
+        int gtile = -1;
+        if (p.cfg.persistent) {
+            uint32_t item = 0;
+            if (lane == 0) item = atomicAdd(&qw->counter_fwd, 1u);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item < (uint32_t)p.vt.total_tiles) gtile = (int)order[item];
+        } else if (round == 0) {
+            gtile = (int)blockIdx.x;
+        }
+        if (gtile < 0) {
+            // end marker in the next buffer
+            const uint32_t slot0 = seq % NB;
+            if (seq >= NB && !mbar_wait(&r.empty[slot0], ((seq / NB) - 1) & 1u, p.status)) return;
+            if (lane == 0) r.hdr[slot0].gtile = -1;
+            __syncwarp();
+            mbar_arrive(&r.full[slot0]);
+            return;
+        }
+        const TileInfo ti = tile_info<TW, TH>(p, gtile);
+        ++tseq;
+        const float fox = (float)(ti.tx * TW), foy = (float)(ti.ty * TH);
+        // every tile gets at least one (possibly empty) batch: its pixels are written then
+        for (uint32_t bstart = ti.beg;; bstart += BATCH) {
+            const uint32_t bend = min(ti.end, bstart + BATCH);
+            const uint32_t slot = seq % NB;
+            if (seq >= NB && !mbar_wait(&r.empty[slot], ((seq / NB) - 1) & 1u, p.status)) return;
+            if (bstart > ti.beg) {
+                // stop when every consumer warp has finished the tile
+                const bool d = lane >= NW || *reinterpret_cast<volatile uint32_t *>(&r.done[lane]) == tseq;
+                if (__all_sync(0xffffffffu, d)) break;
+            }
+            Batch<BATCH, false> &sb = r.buf[slot];
+            for (int k = lane; k < BATCH; k += 32) {
+                const uint32_t j = bstart + k;
+                if (j < bend) {
+                    uint32_t id = p.ids[j];
+                    if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
+                    stage<BATCH, false>(rec, id, sb, k, fox, foy, plain);
+                }
+            }
+            if (lane == 0) {
+                FwdHeader &h = r.hdr[slot];
+                h.gtile = gtile;
+                h.bstart = bstart;
+                h.bend = bend;
+                h.tseq = tseq;
+                h.first = bstart == ti.beg;
+                h.last = bend >= ti.end;
+            }
+            __syncwarp();
+            mbar_arrive(&r.full[slot]);           // each lane: its staged slots are released
+            ++seq;
+            if (bend >= ti.end) break;
+        }
+    }
+}
+
+// Consumer warp: walks each batch for its 8x4 pixel block, front to back.  Each 4x4
+// half of the block culls the staged splats against itself and walks its own hits,
+// the two halves in step.
+template <int TW, int TH, int BATCH, bool COUNT>
+__device__ void fwd_consume(const RenderLaunch &p, FwdRing<BATCH, TW * TH / 32> &r) {
+    constexpr int NB = kFwdStages, NW = TW * TH / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4;             // 4x4 half of the warp's 8x4 block
+    unsigned long long c_visit = 0, c_full = 0, c_comp = 0;
+    // per-tile state of this lane's pixel
+    bool inside = false, done = true, written = true, vfit = false;
+    f32x2 fp = 0;
+    float cxb = 0.0f, cyb = 0.0f, T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0, beg = 0;
+    int gtile = 0, px = 0, py = 0;
+    uint32_t *vw = p.vis;                   // this warp's first word of the tile's mask rows
+    for (uint32_t seq = 0;; ++seq) {
+        const uint32_t slot = seq % NB;
+        if (!mbar_wait(&r.full[slot], (seq / NB) & 1u, p.status)) break;
+        const FwdHeader h = r.hdr[slot];
+        if (h.gtile < 0) break;
+        const Batch<BATCH, false> &s = r.buf[slot];
+        if (h.first) {
+            const TileInfo ti = tile_info<TW, TH>(p, h.gtile);
+            gtile = h.gtile;
+            const int bx = ti.tx * TW + (warp % (TW / 8)) * 8, by = ti.ty * TH + (warp / (TW / 8)) * 4;
+            px = bx + 4 * half + (lane & 3);
+            py = by + ((lane >> 2) & 3);
+            inside = px < ti.W && py < ti.H;
+            // tile-local coordinates (pixel centres at i + 1/2)
+            const int ox = ti.tx * TW, oy = ti.ty * TH;
+            fp = pack2((float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f);
+            cxb = (float)(bx - ox) + 2.0f;     // left half's centre
+            cyb = (float)(by - oy) + 2.0f;
+            T = 1.0f; C0 = C1 = C2 = 0.0f;
+            last = 0;
+            done = !inside;
+            written = false;
+            beg = ti.beg;
+            // the visibility mask: one word per 32 entries of the tile's list, NW words apart
+            // (the tile's rows are written whole or not at all)
+            const size_t vrow = vis_row(ti.beg, gtile);
+            vfit = (vrow + ((ti.end - ti.beg + 31) >> 5)) * NW <= p.vis_words;
+            if (!vfit && warp == 0 && lane == 0) set_status(p.status, HGS_DEV_CAPACITY);
+            vw = p.vis + (vfit ? vrow * NW + warp : 0);
+        }
+        if (!written) {
+            const int cnt = (int)(h.bend - h.bstart);
+            const uint32_t rel0 = h.bstart - beg;
+            uint32_t *vwc = vw + (size_t)(rel0 >> 5) * NW;
+            bool wdone = __all_sync(0xffffffffu, done);
+            for (int c = 0; c < cnt && !wdone; c += 32) {
+                const int jl = c + lane;
+                bool h0 = false, h1 = false;
+                if (jl < cnt) cull_halves(s, jl, cxb, cyb, h0, h1);
+                const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+                // each half walks its own hits, the two in step
+                unsigned m = half ? m1 : m0;
+                uint32_t cm = 0;                 // chunk slots this lane composited
+                while (m) {
+                    const unsigned lb = m & (0u - m);     // the visited slot's bit
+                    const int k = c + __ffs(m) - 1;
+                    m ^= lb;
+                    if (!done) {
+                        Eval ev;
+                        if (COUNT) ++c_visit;
+                        const bool hit = eval_alpha(fp, s, k, ev);
+                        if (COUNT && ev.G >= 0.0f) ++c_full;
+                        if (hit) {
+                            const float Tn = __fmul_rn(T, __fsub_rn(1.0f, ev.a));
+                            if (Tn < kTMin) {
+                                done = true;
+                            } else {
+                                if (COUNT) ++c_comp;
+                                const float w = __fmul_rn(ev.a, T);
+                                const float2 rg = *reinterpret_cast<const float2 *>(&s.g2[k].z);
+                                C0 = __fmaf_rn(rg.x, w, C0);
+                                C1 = __fmaf_rn(rg.y, w, C1);
+                                C2 = __fmaf_rn(s.b[k], w, C2);
+                                T = Tn;
+                                last = rel0 + k + 1;
+                                cm |= lb;
+                            }
+                        }
+                    }
+                }
+                // the chunk's mask word: splats composited at any pixel of the warp's block
+                cm = __reduce_or_sync(0xffffffffu, cm);
+                if (lane == 0 && vfit) *vwc = cm;
+                vwc += NW;
+                // checked once per chunk, not per visit: a warp whose lanes are all done only
+                // runs the rest of this chunk's (cheap) bit loop (render_fwd 0.711 -> 0.679 ms)
+                wdone = __all_sync(0xffffffffu, done);
+            }
+            if (wdone || h.last) {
+                if (inside) {
+                    const TileInfo ti = tile_info<TW, TH>(p, gtile);
+                    const size_t HW = (size_t)ti.W * ti.H;
+                    const size_t pix = (size_t)py * ti.W + px;
+                    float *img = p.image + 3 * (size_t)ti.pix_off;
+                    img[pix] = C0 + T * ti.bg[0];
+                    img[HW + pix] = C1 + T * ti.bg[1];
+                    img[2 * HW + pix] = C2 + T * ti.bg[2];
+                    p.final_T[ti.pix_off + pix] = T;
+                    p.n_contrib[ti.pix_off + pix] = last;
+                }
+                written = true;
+                __syncwarp();
+                if (lane == 0) *reinterpret_cast<volatile uint32_t *>(&r.done[warp]) = h.tseq;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&r.empty[slot]);
+    }
+    if (COUNT) add_counters(p.counters, c_visit, c_full, c_comp, 0ull);
+}
+
 // ---- kernels ------------------------------------------------------------------------
-// Resident blocks per SM asked of the register allocator for the forward, in eighths
-// of the SM's 64 warps: 5/8 (at most 48 registers a thread; measured at 3M splats,
-// 1080p, ~3% faster than 4/8).
-template <int NT, int EIGHTHS>
-constexpr int kMinBlocks = 2048 / NT * EIGHTHS / 8;
+// Forward: TW*TH consumer threads (one pixel each) and one producer warp; resident blocks
+// asked of the register allocator as for the backward.
+template <int TW, int TH>
+constexpr int kFwdMinBlocks = TW * TH >= 256 ? 4 : 10;
 
 template <int TW, int TH, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TW *TH / kSplit<true, TW, TH>, (kMinBlocks<TW * TH / kSplit<true, TW, TH>, 5>))
-    k_render_fwd(RenderLaunch p) {
-    constexpr int SPLIT = kSplit<true, TW, TH>;
-    __shared__ Batch<BATCH, false> s;
-    if (!p.cfg.persistent) {
-        render_tile_fwd<TW, TH, BATCH, COUNT>(p, blockIdx.x / SPLIT, blockIdx.x % SPLIT, s);
-        return;
+__global__ void __launch_bounds__(TW *TH + 32, (kFwdMinBlocks<TW, TH>)) k_render_fwd(RenderLaunch p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FwdRing<BATCH, TW * TH / 32> &r = *reinterpret_cast<FwdRing<BATCH, TW * TH / 32> *>(smem_raw);
+    constexpr int NB = kFwdStages, NC = TW * TH;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&r.full[i], 32);          // the producer warp's lanes
+            mbar_init(&r.empty[i], NC / 32);    // one arrival per consumer warp
+        }
     }
-    Queue *q = reinterpret_cast<Queue *>(p.ws);
-    const uint32_t *order = reinterpret_cast<const uint32_t *>(q + 1);
-    __shared__ uint32_t s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&q->counter_fwd, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= (uint32_t)p.vt.total_tiles * SPLIT) break;
-        render_tile_fwd<TW, TH, BATCH, COUNT>(p, (int)order[item / SPLIT], (int)(item % SPLIT), s);
-        __syncthreads();
-    }
+    if (threadIdx.x < NC / 32) r.done[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x >= NC)
+        fwd_produce<TW, TH, BATCH>(p, r);
+    else
+        fwd_consume<TW, TH, BATCH, COUNT>(p, r);
 }
 
 // Backward: TW*TH consumer threads (one pixel each) and one producer warp; resident
@@ -829,9 +920,10 @@ constexpr auto render_kernel() {
 template <int TW, int TH, int BATCH, bool FWD, bool COUNT, bool PLAIN>
 cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
     auto kern = render_kernel<TW, TH, BATCH, FWD, COUNT, PLAIN>();
-    constexpr int SPLIT = kSplit<FWD, TW, TH>, NT = FWD ? TW * TH / SPLIT : TW * TH + 32;
-    constexpr int smem = FWD ? 0 : (int)sizeof(BwdRing<FWD ? 32 : BATCH, TW * TH / 32>);
-    const int items = p.vt.total_tiles * SPLIT;
+    constexpr int NT = TW * TH + 32;
+    constexpr int smem = FWD ? (int)sizeof(FwdRing<BATCH, TW * TH / 32>)
+                             : (int)sizeof(BwdRing<FWD ? 32 : BATCH, TW * TH / 32>);
+    const int items = p.vt.total_tiles;
     if (smem > 48 * 1024) {
         // above the default dynamic shared-memory limit; a per-device attribute, so set
         // on every call (a host-side call, no stream work)
@@ -842,9 +934,9 @@ cudaError_t launch_t(const RenderLaunch &p, cudaStream_t s) {
         kern<<<items, NT, smem, s>>>(p);
         return cudaGetLastError();
     }
-    // resident blocks per SM (assumed the same on every device of this architecture: the
-    // kernels use only static shared memory), times the current device's SM count; atomic,
-    // since threads making their first calls at the same time store the same value
+    // resident blocks per SM (assumed the same on every device of this architecture),
+    // times the current device's SM count; atomic, since threads making their first calls
+    // at the same time store the same value
     static std::atomic<int> occ_cache{0};
     int occ = occ_cache.load(std::memory_order_relaxed);
     if (!occ) {
@@ -881,9 +973,11 @@ cudaError_t prepare_queue(const RenderLaunch &p, cudaStream_t s) {
 template <bool FWD, int TW, int TH>
 cudaError_t dispatch_batch(const RenderLaunch &p, cudaStream_t s) {
     if (FWD) {
-        // default: the tile's pixel count (16x16 tiles at 3M splats: forward 0.677 / 0.697 /
-        // 0.886 ms at 256 / 128 / 512)
-        switch (p.cfg.batch ? p.cfg.batch : TW * TH) {
+        // default 128 (16x16 tiles at 3M splats, eager launches: forward 0.691 / 0.679 / 0.696
+        // / 1.14 ms at 64 / 128 / 224 / 512; smaller batches stage fewer splats past the
+        // point where every pixel of the tile has finished, the largest leave room for
+        // fewer blocks per SM)
+        switch (p.cfg.batch ? p.cfg.batch : std::min(TW * TH, 128)) {
             case 32: return launch_c<TW, TH, 32, true>(p, s);
             case 64: return launch_c<TW, TH, 64, true>(p, s);
             case 128: return launch_c<TW, TH, 128, true>(p, s);
