@@ -171,7 +171,8 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
     n2 = n2 + qy * qy;
     n2 = n2 + qz * qz;
     float qn = sqrtf(n2);
-    float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
+    float iq = 1.0f / qn;
+    float w = qw * iq, x = qx * iq, y = qy * iq, z = qz * iq;
 
     /* 2. rotation matrix */
     float R[3][3];
@@ -207,7 +208,8 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
     if (!(t[2] > (float)cam->near_plane)) return;
 
     /* 6. clamped x/z, y/z */
-    float ux = t[0] / t[2], uy = t[1] / t[2];
+    float iz = 1.0f / t[2];
+    float ux = t[0] * iz, uy = t[1] * iz;
     float uxc = ux, uyc = uy;
     if (o->fov_clamp) {
         float limx = 1.3f * ((0.5f * W) / fx);
@@ -217,10 +219,10 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
     }
 
     /* 7. Jacobian entries */
-    float j00 = fx / t[2];
-    float j02 = -((fx * uxc) / t[2]);
-    float j11 = fy / t[2];
-    float j12 = -((fy * uyc) / t[2]);
+    float j00 = fx * iz;
+    float j02 = -((fx * uxc) * iz);
+    float j11 = fy * iz;
+    float j12 = -((fy * uyc) * iz);
 
     /* 8. M = J W_rot (2x3) */
     float M[2][3];
@@ -262,8 +264,8 @@ static void canon_bin(const double *mean, const double *scale, const double *qua
     float r = ceilf(3.0f * sqrtf(lam));
 
     /* 13. projected centre */
-    float mux = fx * (t[0] / t[2]) + cx;
-    float muy = fy * (t[1] / t[2]) + cy;
+    float mux = fx * ux + cx;
+    float muy = fy * uy + cy;
     out->mux = mux; out->muy = muy; out->radius = r;
 
     /* 14. finiteness cull */

@@ -12,7 +12,9 @@ import json
 import math
 import os
 
-CANDIDATES = [((16, 16), 256), ((16, 16), 128), ((32, 8), 256), ((32, 8), 128), ((8, 8), 128), ((8, 8), 64)]
+# (tile shape, batch): batch 0 takes each compositing kernel's own default (forward 128
+# splats, or 64 at 8x8; backward 224, or 64 at 8x8), a non-zero batch is used by both
+CANDIDATES = [((16, 16), 0), ((16, 16), 128), ((32, 8), 0), ((32, 8), 128), ((8, 8), 0), ((8, 8), 128)]
 
 
 def n_bucket(n: int) -> int:
@@ -25,7 +27,9 @@ def cache_key(gpu_name: str, n: int, sizes, persistent: bool) -> str:
     for w, h in sizes:
         hist[f"{w}x{h}"] = hist.get(f"{w}x{h}", 0) + 1
     views = ",".join(f"{k}:{v}" for k, v in sorted(hist.items()))
-    return f"{gpu_name}|n~{n_bucket(n)}|{views}|{'persistent' if persistent else 'per-tile'}"
+    # the candidate set is part of the key: a choice made among other candidates is stale
+    cands = ";".join(f"{t[0]}x{t[1]}/{b}" for t, b in CANDIDATES)
+    return f"{gpu_name}|n~{n_bucket(n)}|{views}|{'persistent' if persistent else 'per-tile'}|{cands}"
 
 
 def load(path):

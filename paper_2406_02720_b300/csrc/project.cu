@@ -164,7 +164,8 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     n2 = fa(n2, fm(q[2], q[2]));
     n2 = fa(n2, fm(q[3], q[3]));
     float qn = __fsqrt_rn(n2);
-    float w = fdv(q[0], qn), x = fdv(q[1], qn), y = fdv(q[2], qn), z = fdv(q[3], qn);
+    const float iq = __frcp_rn(qn);
+    float w = fm(q[0], iq), x = fm(q[1], iq), y = fm(q[2], iq), z = fm(q[3], iq);
     // 2. rotation
     float R[3][3];
     R[0][0] = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
@@ -194,7 +195,8 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     // 5. near-plane cull
     if (!(t[2] > cam.near_plane)) return;
     // 6. clamped x/z, y/z
-    float ux = fdv(t[0], t[2]), uy = fdv(t[1], t[2]);
+    const float iz = __frcp_rn(t[2]);
+    float ux = fm(t[0], iz), uy = fm(t[1], iz);
     float uxc = ux, uyc = uy;
     if (fov_clamp) {
         float limx = fm(1.3f, fdv(fm(0.5f, (float)cam.width), cam.fx));
@@ -203,10 +205,10 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
         uyc = fminf(fmaxf(uy, -limy), limy);
     }
     // 7. Jacobian
-    float j00 = fdv(cam.fx, t[2]);
-    float j02 = -fdv(fm(cam.fx, uxc), t[2]);
-    float j11 = fdv(cam.fy, t[2]);
-    float j12 = -fdv(fm(cam.fy, uyc), t[2]);
+    float j00 = fm(cam.fx, iz);
+    float j02 = -fm(fm(cam.fx, uxc), iz);
+    float j11 = fm(cam.fy, iz);
+    float j12 = -fm(fm(cam.fy, uyc), iz);
     // 8. M = J W
     float M[2][3];
 #pragma unroll
@@ -245,8 +247,8 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     float lam = fa(mid, __fsqrt_rn(fmaxf(0.1f, fs(fm(mid, mid), det))));
     float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
     // 13. centre
-    float mux = fa(fm(cam.fx, fdv(t[0], t[2])), cam.cx);
-    float muy = fa(fm(cam.fy, fdv(t[1], t[2])), cam.cy);
+    float mux = fa(fm(cam.fx, ux), cam.cx);
+    float muy = fa(fm(cam.fy, uy), cam.cy);
     o.mux = mux; o.muy = muy;
     // 14. finiteness
     if (!(isfinite(mux) && isfinite(muy) && isfinite(r))) return;
@@ -378,11 +380,12 @@ __device__ __forceinline__ void canon_project(const float m[3], const float s[3]
     }
     // 16. tile rect
     int tiles_x = div_up(cam.width, tw), tiles_y = div_up(cam.height, th);
-    float ftw = (float)tw, fth = (float)th;
-    float x0 = floorf(fdv(fs(mux, ex0), ftw));
-    float x1 = fa(floorf(fdv(fa(mux, ex1), ftw)), 1.0f);
-    float y0 = floorf(fdv(fs(muy, ey0), fth));
-    float y1 = fa(floorf(fdv(fa(muy, ey1), fth)), 1.0f);
+    // the tile sizes are powers of two, so x * (1/t) rounds to the same value as x / t
+    const float itw = __frcp_rn((float)tw), ith = __frcp_rn((float)th);
+    float x0 = floorf(fm(fs(mux, ex0), itw));
+    float x1 = fa(floorf(fm(fa(mux, ex1), itw)), 1.0f);
+    float y0 = floorf(fm(fs(muy, ey0), ith));
+    float y1 = fa(floorf(fm(fa(muy, ey1), ith)), 1.0f);
     x0 = fminf(fmaxf(x0, 0.0f), (float)tiles_x);
     x1 = fminf(fmaxf(x1, 0.0f), (float)tiles_x);
     y0 = fminf(fmaxf(y0, 0.0f), (float)tiles_y);
