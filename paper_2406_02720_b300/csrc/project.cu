@@ -23,7 +23,7 @@
 // are FP32, with FP64 only for near-degenerate splats: in the forward, a splat
 // whose plane nearly contains the ray (v < 1e-3 var_s) gets its half-plane terms
 // w' recomputed in FP64; in the adjoint, such a splat and a splat whose hat Sigma
-// is ill-conditioned (condition number above 300) get their geometry adjoint
+// is ill-conditioned (condition number above 150) get their geometry adjoint
 // (conic, covariance, half-plane terms to mean, scale, rotation, normal) in FP64.
 #include <math.h>
 
@@ -43,11 +43,12 @@ enum { MODE_CULLED = 0, MODE_NORMAL = 1, MODE_STEP = 2, MODE_HALF = 3 };
 // splitting plane nearly contains the ray (v < kVRelFp64 * var_s).
 constexpr float kVRelFp64 = 1e-3f;
 // The projection adjoint also takes the FP64 path for a splat whose hat Sigma has a
-// condition number above kCondFp64 (a needle- or disk-like footprint, ~0.3% of the
-// splats of the benchmark scenes): through the conic, dL/d hat Sigma = -conic G conic
+// condition number above kCondFp64 (a needle- or disk-like footprint, ~0.9% of the
+// splats of the 3M-splat scene): through the conic, dL/d hat Sigma = -conic G conic
 // loses about cond x u in binary32, which reached 1e-3..3e-2 of the scale and
-// quaternion gradients of such splats.
-constexpr float kCondFp64 = 300.0f;
+// quaternion gradients of such splats (1.2e-3 at a condition number of 242; with the
+// cut at 150 instead of 300 the projection adjoint takes 0.347 -> 0.351 ms).
+constexpr float kCondFp64 = 150.0f;
 constexpr float kCondFp64Test = (1.0f + kCondFp64) * (1.0f + kCondFp64) / kCondFp64;
 // Scale applied to w in step mode (v ~ 0): P becomes a step at w.d = 0.
 constexpr float kStepScale = 1.2089258196146292e24f;   // 2^80

@@ -44,7 +44,7 @@
 // bounded waits; 1.318 -> 1.294 ms against block-synchronous batches).
 // The 12 screen-space gradients of a (warp, splat) leave as per-lane float4
 // atomic adds, with one shuffle level folding lane pairs first when more than 12
-// lanes contribute.
+// lanes contribute, and a second when more than 16 do.
 //
 // Persistent mode (the default): a grid of resident blocks pops tiles from an
 // atomic queue whose order is heaviest-first (bucketed by list length).
@@ -317,9 +317,13 @@ struct Queue {
 // atomics: 24 instructions instead of a full 5-level reduction (~62), at the price of
 // more atomic traffic, which the L2 absorbs (measured: fastest of full reduction,
 // direct atomics from up to 1..32 lanes, and this split; at 3M splats, 1080p the
-// backward takes 1.333 / 1.325 / 1.322 / 1.327 / 1.393 ms folding above 8 / 10 / 12 /
-// 16 / 24 contributing lanes).
+// backward took 1.333 / 1.325 / 1.322 / 1.327 / 1.393 ms folding above 8 / 10 / 12 /
+// 16 / 24 contributing lanes, before the visibility mask; with it, 1.215 / 1.206 /
+// 1.217 ms above 8 / 12 / 16 and 1.606 ms with no fold).  Above kFold2Above lanes a
+// second level folds lane l + 8 into lane l, so at most 8 lanes add to the same splat
+// (1.206 -> 1.169 ms; 1.171 ms above 20 lanes; a third level above 28 lanes, 1.184).
 constexpr int kFoldAbove = 12;
+constexpr int kFold2Above = 16;
 __device__ __forceinline__ void atomic_add12(float *dst, const float g[12]) {
     float4 *d4 = reinterpret_cast<float4 *>(dst);
     atomicAdd(d4, make_float4(g[0], g[1], g[2], g[3]));
@@ -598,7 +602,18 @@ __device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
                         const f32x2 o = pack2(__shfl_xor_sync(0xffffffffu, x0, 16), __shfl_xor_sync(0xffffffffu, x1, 16));
                         unpack2(add2(pack2(x0, x1), o), gr[f], gr[f + 1]);
                     }
-                    if (lane < 16 && ((any >> lane) & 0x10001u)) atomic_add12(dst, gr);
+                    if (__popc(any) > kFold2Above) {
+                        // lane l + 8 into lane l: lanes 0..7 then hold four pixels each
+#pragma unroll
+                        for (int f = 0; f < 12; f += 2) {
+                            const f32x2 o = pack2(__shfl_xor_sync(0xffffffffu, gr[f], 8),
+                                                  __shfl_xor_sync(0xffffffffu, gr[f + 1], 8));
+                            unpack2(add2(pack2(gr[f], gr[f + 1]), o), gr[f], gr[f + 1]);
+                        }
+                        if (lane < 8 && ((any >> lane) & 0x01010101u)) atomic_add12(dst, gr);
+                    } else if (lane < 16 && ((any >> lane) & 0x10001u)) {
+                        atomic_add12(dst, gr);
+                    }
                 }
             }
         }
