@@ -230,7 +230,8 @@ def run_gpu(args):
     # ---- work counters for the roofline (one extra forward, not timed) ------------------
     stats = rast.stats(dL)
     alu = measure_alu_peaks(dev)
-    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks, alu)
+    dpasses = depth_sort_passes(rast.depth.cpu().numpy(), rast.tiles.cpu().numpy())
+    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks, alu, dpasses)
 
     # ---- end to end through host buffers --------------------------------------------------
     e2e = run_e2e(args, rast, g, dL, grads, pixels, dev)
@@ -254,7 +255,8 @@ def run_gpu(args):
                                    "all-reduce in 'sharded'"),
                    "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
         "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
-        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles, alu),
+        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles, alu, dpasses),
+        "depth_sort_passes": dpasses,
         "alu_peaks": alu,
         "clocks": clocks,
         "e2e": e2e, "e2e_params_over_pcie": e2e_full, "gpu_launches": launches * args.steps,
@@ -286,15 +288,29 @@ def tile_bits(total_tiles):
     return bits
 
 
-def n_sort_passes(total_tiles):
-    """8-bit radix passes: four over the per-splat depth keys, then ceil(tile bits / 8)
-    over the u32 tile ids of the depth-ordered pairs."""
-    return 4, (tile_bits(total_tiles) + 7) // 8
+def n_sort_passes(total_tiles, depth_passes=4):
+    """8-bit radix passes: depth_passes over the per-splat depth keys (at most four),
+    then ceil(tile bits / 8) over the u32 tile ids of the depth-ordered pairs."""
+    return depth_passes, (tile_bits(total_tiles) + 7) // 8
+
+
+def depth_sort_passes(depth, tiles):
+    """Depth passes the binning runs for these projected depths (float32) and tiles
+    touched: the valid keys (bits of the depths of drawn splats) are sorted as
+    key - min, the culled ones just above the range, so ceil(bits(max - min + 1) / 8)
+    passes (0 with no drawn splat)."""
+    import numpy as np
+    k = np.asarray(depth, np.float32).view(np.uint32)[np.asarray(tiles) > 0]
+    if k.size == 0:
+        return 0
+    r = int(k.max()) - int(k.min()) + 1
+    return (r.bit_length() + 7) // 8
 
 
 def launches_per_step(total_tiles, persistent=False):
     """Kernels of one fwd+bwd step: k_project + k_project_fp64; binning =
-    k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep),
+    k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep; all four
+    depth passes are launched, those past the keys' range return at once),
     k_scan_reduce, k_chunk_scan, k_duplicate, k_ranges; k_render_fwd and k_render_bwd,
     each after k_queue_count + k_queue_fill when persistent; k_project_bwd +
     k_project_bwd_fp64."""
@@ -302,20 +318,21 @@ def launches_per_step(total_tiles, persistent=False):
     return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + 2 * (3 if persistent else 1) + 2
 
 
-def alg_bytes(n, n_pairs, total_tiles):
+def alg_bytes(n, n_pairs, total_tiles, depth_passes=4):
     """Bytes each memory-bound phase must move in this design (per launch sequence):
       project     : 252 B parameters read (mean 12, scale 12, quat 16, normal 12,
                     opacities 8, SH 192) + 88 B written (record 64, depth 4, rect 16,
                     tiles 4) per splat
-      bin         : per splat: depth keys 16 (read depth+tiles, write key+id), 4 depth
-                    passes x 20 (upsweep reads 4, downsweep reads 8 writes 8), scan 12
+      bin         : per splat: depth keys 16 (read depth+tiles, write key+id), one to
+                    four depth passes (as the keys' range needs) x 20 (upsweep reads 4,
+                    downsweep reads 8 writes 8), scan 12
                     (read order + tiles, write tiles in depth order), duplicate 24
                     (order, tiles in depth order, rect);
                     per pair: 8 written by duplicate, 20 per tile pass, 4 read by ranges;
                     8 per tile written by ranges
       project_bwd : 252 B parameters + 48 B screen-space gradients read, 252 B written
     """
-    dp, tp = n_sort_passes(total_tiles)
+    dp, tp = n_sort_passes(total_tiles, depth_passes)
     return {"project": n * (252 + 88),
             "bin": n * (16 + 20 * dp + 12 + 24) + n_pairs * (8 + 20 * tp + 4) + total_tiles * 8,
             "project_bwd": n * (252 + 48 + 252)}
@@ -416,7 +433,7 @@ def alu_peaks(measured):
             f"computed: 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz")
 
 
-def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None):
+def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None, depth_passes=4):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     src = "of measured" if hbm else "of fallback"
@@ -439,20 +456,20 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None):
         out.update({"traffic": profiled_traffic(dom), "frac_fp32": f_fp32, "frac_mufu": f_mufu,
                     "note": f"peak {peak_src}; algorithmic ops = counted events x ops per event"})
     else:
-        b = alg_bytes(n, n_pairs, total_tiles).get(dom, 0)
+        b = alg_bytes(n, n_pairs, total_tiles, depth_passes).get(dom, 0)
         ach = b / (phases[dom] * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": None, "note": src})
     return out
 
 
-def phase_rooflines(phases, stats, n_pairs, n, total_tiles, measured=None):
+def phase_rooflines(phases, stats, n_pairs, n, total_tiles, measured=None, depth_passes=4):
     """HBM fraction of the memory-bound phases and ALU fractions of the compositing
     phases (each against its own bound; algorithmic bytes/ops per launch)."""
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6400.0)
     out = {}
-    for k, b in alg_bytes(n, n_pairs, total_tiles).items():
+    for k, b in alg_bytes(n, n_pairs, total_tiles, depth_passes).items():
         out[k] = {"bound": "hbm", "GBs": b / (phases[k] * 1e-3) / 1e9, "frac": b / (phases[k] * 1e-3) / 1e9 / hbm}
     fp32_peak, mufu_peak, _ = alu_peaks(measured)
     for key, ph in (("fwd", "render_fwd"), ("bwd", "render_bwd")):

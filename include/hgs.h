@@ -221,7 +221,8 @@ hgs_status hgs_project(const hgs_gaussians *g, const hgs_camera *cams_host,
  * ascending value order (value = view*n + splat), and per-tile [start, end)
  * ranges (ranges[2*t], ranges[2*t+1]; [0,0) for an empty tile).  This is the
  * stable LSD radix sort (8-bit digits) of the keys over the bits in use; its
- * four passes over the depth half run on the n_views*n per-splat depths before
+ * passes over the depth half (as many 8-bit passes as the drawn splats' depth
+ * range needs, at most four) run on the n_views*n per-splat depths before
  * the splats are expanded into their tiles, which gives the same order.
  *   keys_out [pair_capacity] uint64, optional (NULL: not written),
  *   ids_out  [pair_capacity] uint32, ranges [2*total_tiles] uint32,

@@ -4,7 +4,8 @@
 // (global tile id << 32) | bits(depth), one per covered tile of every
 // (view, splat), emitted in (view, splat) order, i.e. the order of the keys with
 // ties broken by the splat index.  It is computed in two stages:
-//   1. the four 8-bit passes over the depth half run on the n_views*n per-splat
+//   1. the 8-bit passes over the depth half (up to four, as many as the drawn splats'
+//      key range needs) run on the n_views*n per-splat
 //      depth keys (culled splats get key 0xFFFFFFFF and sort last) -- duplicating
 //      a splat into its tiles commutes with a stable sort on depth, so these
 //      passes need not touch the much longer pair list;
@@ -39,8 +40,38 @@ constexpr int kGroup = kBlock / 32;          // chunks of kBlock splats per scan
 
 struct Ctrl {                                // zeroed at the start of every call
     uint32_t totals[kRadix];                 // per-digit totals of the current pass
-    uint32_t pad[64];
+    uint32_t kmin_inv, kmax;                 // ~(smallest) and largest valid depth key
+    uint32_t pad[62];
 };
+
+// Depth passes actually needed: the valid depth keys (bits of positive floats, so
+// ordered as integers) are sorted as key - kmin and the culled ones as R = kmax - kmin
+// + 1, after every valid key; the order is the same as that of the raw keys, and
+// ceil(bits(R) / 8) passes of 8 bits cover it (3 instead of 4 when every depth lies
+// within a factor of about 2-4 of the nearest, as in a scene seen from outside).
+// The first pass reads raw keys and writes shifted ones; passes past the count return
+// at once, and the sorted order ends in the A buffers after an even count, else in B.
+struct DepthPlan {
+    int passes;
+    uint32_t kmin, culled;
+};
+__device__ __forceinline__ DepthPlan depth_plan(const Ctrl *c) {
+    DepthPlan d;
+    d.kmin = ~c->kmin_inv;
+    const uint32_t kmax = c->kmax;
+    if (d.kmin > kmax) {                     // no valid key: the identity order
+        d.passes = 0;
+        d.kmin = 0;
+        d.culled = 0;
+        return d;
+    }
+    d.culled = kmax - d.kmin + 1u;
+    d.passes = (32 - __clz(d.culled) + kRadixBits - 1) / kRadixBits;
+    return d;
+}
+__device__ __forceinline__ uint32_t depth_key(const DepthPlan &d, uint32_t raw) {
+    return raw == 0xffffffffu ? d.culled : raw - d.kmin;
+}
 
 struct Ws {
     Ctrl *ctrl;
@@ -112,24 +143,43 @@ struct Count {
 // ---- stage 1: depth keys ------------------------------------------------------------------
 // Four (view, splat) entries a thread, with 128-bit loads and stores (vn % 4 tail
 // handled element by element).
+// The block's smallest and largest valid key go to ctrl (one atomic each per block).
 __global__ void __launch_bounds__(kBlock) k_depth_keys(const uint32_t *__restrict__ tiles,
                                                        const float *__restrict__ depth, long long vn,
-                                                       uint32_t *__restrict__ dk, uint32_t *__restrict__ dv) {
+                                                       uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
+                                                       Ctrl *ctrl) {
+    __shared__ uint32_t s_min[kBlock / 32], s_max[kBlock / 32];
     const long long i0 = 4 * ((long long)blockIdx.x * kBlock + threadIdx.x);
-    if (i0 >= vn) return;
+    uint32_t kmin_inv = 0, kmax = 0;      // ~min and max of this thread's valid keys
     if (i0 + 4 <= vn) {
         const uint4 t = *reinterpret_cast<const uint4 *>(tiles + i0);
         const float4 d = *reinterpret_cast<const float4 *>(depth + i0);
-        *reinterpret_cast<uint4 *>(dk + i0) =
-            make_uint4(t.x ? __float_as_uint(d.x) : 0xffffffffu, t.y ? __float_as_uint(d.y) : 0xffffffffu,
-                       t.z ? __float_as_uint(d.z) : 0xffffffffu, t.w ? __float_as_uint(d.w) : 0xffffffffu);
+        const uint4 k = make_uint4(t.x ? __float_as_uint(d.x) : 0xffffffffu, t.y ? __float_as_uint(d.y) : 0xffffffffu,
+                                   t.z ? __float_as_uint(d.z) : 0xffffffffu, t.w ? __float_as_uint(d.w) : 0xffffffffu);
+        *reinterpret_cast<uint4 *>(dk + i0) = k;
         const uint32_t b = (uint32_t)i0;
         *reinterpret_cast<uint4 *>(dv + i0) = make_uint4(b, b + 1, b + 2, b + 3);
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (kk[j] != 0xffffffffu) { kmin_inv = max(kmin_inv, ~kk[j]); kmax = max(kmax, kk[j]); }
     } else {
         for (long long i = i0; i < vn; ++i) {
-            dk[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
+            const uint32_t k = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
+            dk[i] = k;
             dv[i] = (uint32_t)i;
+            if (k != 0xffffffffu) { kmin_inv = max(kmin_inv, ~k); kmax = max(kmax, k); }
         }
+    }
+    kmin_inv = __reduce_max_sync(0xffffffffu, kmin_inv);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_min[warp] = kmin_inv; s_max[warp] = kmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w2 = 1; w2 < kBlock / 32; ++w2) { kmin_inv = max(kmin_inv, s_min[w2]); kmax = max(kmax, s_max[w2]); }
+        if (kmin_inv) atomicMax(&ctrl->kmin_inv, kmin_inv);
+        if (kmax) atomicMax(&ctrl->kmax, kmax);
     }
 }
 
@@ -137,9 +187,18 @@ __global__ void __launch_bounds__(kBlock) k_depth_keys(const uint32_t *__restric
 // Each thread counts 16 consecutive keys, fetched with four 128-bit loads that are
 // all in flight at once (the counts of a partition do not depend on the order in
 // which its keys are visited).
+// plan (depth passes only, else null): skip a pass past the plan's count; the first
+// pass shifts the raw keys (depth_key).
 __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__ keys, Count cnt, int shift,
-                                                    uint32_t *__restrict__ counts, size_t stride) {
+                                                    uint32_t *__restrict__ counts, size_t stride,
+                                                    const Ctrl *plan, int pass) {
     __shared__ uint32_t s_cnt[kBlock / 32][kRadix];
+    DepthPlan dp{};
+    if (plan) {
+        dp = depth_plan(plan);
+        if (pass >= dp.passes) return;
+    }
+    const bool shift_keys = plan && pass == 0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     const uint32_t K = cnt.get();
     const uint32_t n_parts = (K + kPart - 1) / kPart;
@@ -161,7 +220,10 @@ __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__
         }
 #pragma unroll
         for (int j = 0; j < kItems; ++j)
-            if (base + j < K) atomicAdd(&s_cnt[warp][(k[j] >> shift) & (kRadix - 1)], 1u);
+            if (base + j < K) {
+                const uint32_t kj = shift_keys ? depth_key(dp, k[j]) : k[j];
+                atomicAdd(&s_cnt[warp][(kj >> shift) & (kRadix - 1)], 1u);
+            }
         __syncthreads();
         uint32_t total = 0;
 #pragma unroll
@@ -177,9 +239,10 @@ __global__ void __launch_bounds__(kBlock) k_upsweep(const uint32_t *__restrict__
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp);
 
 __global__ void __launch_bounds__(kBlock) k_digit_scan(uint32_t *__restrict__ counts, Count cnt, size_t stride,
-                                                       Ctrl *ctrl) {
+                                                       Ctrl *ctrl, bool depth, int pass) {
     __shared__ uint32_t s_tmp[kBlock / 32];
     __shared__ uint32_t s_total;
+    if (depth && pass >= depth_plan(ctrl).passes) return;
     const int d = blockIdx.x;
     const uint32_t K = cnt.get();
     const uint32_t n_parts = (K + kPart - 1) / kPart;
@@ -239,6 +302,8 @@ struct DownArgs {
     const uint32_t *offsets;         // [256][stride] exclusive per-digit offsets of each partition
     size_t stride;
     const Ctrl *ctrl;
+    bool depth_stage;                // a depth pass: skipped past the plan's count, the first shifts the keys
+    int pass;
     int *status;
 };
 
@@ -273,6 +338,12 @@ template <bool COMPOSE>
 __global__ void __launch_bounds__(kBlock, 4) k_downsweep(DownArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DownSmem &sm = *reinterpret_cast<DownSmem *>(smem_raw);
+    DepthPlan dp{};
+    if (a.depth_stage) {
+        dp = depth_plan(a.ctrl);
+        if (a.pass >= dp.passes) return;
+    }
+    const bool shift_keys = a.depth_stage && a.pass == 0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     const uint32_t K = a.cnt.get();
     const uint32_t n_parts = (K + kPart - 1) / kPart;
@@ -289,6 +360,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_downsweep(DownArgs a) {
             const uint32_t idx = pbase + warp * (32 * kItems) + it * 32 + lane;
             const bool valid = idx < K;
             key[it] = valid ? a.kin[idx] : 0u;
+            if (shift_keys && valid) key[it] = depth_key(dp, key[it]);
             val[it] = valid ? a.vin[idx] : 0u;
         }
 #pragma unroll
@@ -365,11 +437,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_downsweep(DownArgs a) {
 constexpr int kReducePer = 8;
 
 __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t *__restrict__ tiles,
-                                                        const uint32_t *__restrict__ order, long long vn,
-                                                        uint32_t *__restrict__ tiles_sorted,
+                                                        const uint32_t *__restrict__ order_a,
+                                                        const uint32_t *__restrict__ order_b, const Ctrl *plan,
+                                                        long long vn, uint32_t *__restrict__ tiles_sorted,
                                                         unsigned long long *__restrict__ chunk_sum,
                                                         unsigned long long *__restrict__ group_sum) {
     __shared__ unsigned long long s_chunk[kGroup];
+    const uint32_t *__restrict__ order = (depth_plan(plan).passes & 1) ? order_b : order_a;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     // this warp's 256 splats start at `base` (chunk base / kBlock); a thread takes 8 consecutive
     const long long base = (long long)blockIdx.x * kBlock * kReducePer + (long long)warp * 32 * kReducePer;
@@ -475,7 +549,8 @@ __global__ void __launch_bounds__(kChunkScanThreads) k_chunk_scan(unsigned long 
 struct DupArgs {
     const uint32_t *tiles_sorted;   // tiles touched, in depth order
     const int4 *rect;
-    const uint32_t *order;          // (view, splat) indices in depth order
+    const uint32_t *order_a, *order_b;   // (view, splat) indices in depth order: in A after an
+    const Ctrl *plan;                    // even number of depth passes, else in B
     const unsigned long long *chunk_sum;   // pair count of each chunk of kBlock splats
     const unsigned long long *group_pre;   // exclusive pair prefix of each group of kGroup chunks
     long long vn;
@@ -494,13 +569,14 @@ __global__ void __launch_bounds__(kBlock) k_duplicate(DupArgs a) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const long long j0 = (long long)blockIdx.x * kBlock + warp * 32;
     const long long j = j0 + lane;
+    const uint32_t *order = (depth_plan(a.plan).passes & 1) ? a.order_b : a.order_a;
     // this chunk's prefix: its group's, plus the chunks before it in the group
     const uint32_t gi = blockIdx.x % kGroup;
     unsigned long long before = lane < (int)gi ? a.chunk_sum[blockIdx.x - gi + lane] : 0ull;
     const unsigned long long gpre = a.group_pre[blockIdx.x / kGroup];
     uint32_t vi = 0, cnt = 0;
     if (j < a.vn) {
-        vi = a.order[j];
+        vi = order[j];
         cnt = a.tiles_sorted[j];
     }
     uint32_t x = cnt;
@@ -611,12 +687,16 @@ int sweep_blocks() { return num_sms() * launch_shapes().sweep; }
 int aux_blocks() { return num_sms() * launch_shapes().aux; }
 
 // One radix pass over cnt elements: upsweep, digit scan, downsweep.
+// depth_pass >= 0: pass number of the depth stage (planned on the device); -1: a pass
+// over the tile keys.
 cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout, uint64_t *kout64,
                        const float *depth, Count cnt, size_t max_elems, int shift, const Ws &w, int *status,
-                       cudaStream_t s) {
+                       int depth_pass, cudaStream_t s) {
     const int parts = (int)std::max<size_t>((max_elems + kPart - 1) / kPart, 1);
-    k_upsweep<<<std::min(parts, aux_blocks()), kBlock, 0, s>>>(kin, cnt, shift, w.counts, w.parts_stride);
-    k_digit_scan<<<kRadix, kBlock, 0, s>>>(w.counts, cnt, w.parts_stride, w.ctrl);
+    const bool dpass = depth_pass >= 0;
+    k_upsweep<<<std::min(parts, aux_blocks()), kBlock, 0, s>>>(kin, cnt, shift, w.counts, w.parts_stride,
+                                                               dpass ? w.ctrl : nullptr, depth_pass);
+    k_digit_scan<<<kRadix, kBlock, 0, s>>>(w.counts, cnt, w.parts_stride, w.ctrl, dpass, depth_pass);
     DownArgs a{};
     a.kin = kin;
     a.vin = vin;
@@ -629,6 +709,8 @@ cudaError_t radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
     a.offsets = w.counts;
     a.stride = w.parts_stride;
     a.ctrl = w.ctrl;
+    a.depth_stage = dpass;
+    a.pass = depth_pass;
     a.status = status;
     const int grid = std::min(parts, sweep_blocks());
     if (kout64)
@@ -662,22 +744,23 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
     if ((e = cudaMemsetAsync(p.ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, s)) != cudaSuccess) return e;
     if (vn == 0) return cudaSuccess;
 
-    // stage 1: depth keys, four passes over them (the order ends in dkA/dvA)
+    // stage 1: depth keys and up to four passes over them (as many as the keys' range
+    // needs, decided on the device; the order ends in dvA after an even count, else dvB)
     k_depth_keys<<<(unsigned)((vn + 4 * kBlock - 1) / (4 * kBlock)), kBlock, 0, s>>>(p.proj->tiles, p.proj->depth,
-                                                                           (long long)vn, w.dkA, w.dvA);
+                                                                           (long long)vn, w.dkA, w.dvA, w.ctrl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const Count cnt_vn{vn, nullptr, vn};
     for (int pass = 0; pass < kDepthPasses; ++pass) {
         const bool even = (pass % 2) == 0;
         e = radix_pass(even ? w.dkA : w.dkB, even ? w.dvA : w.dvB, even ? w.dkB : w.dkA, even ? w.dvB : w.dvA,
-                       nullptr, nullptr, cnt_vn, vn, kRadixBits * pass, w, p.status, s);
+                       nullptr, nullptr, cnt_vn, vn, kRadixBits * pass, w, p.status, pass, s);
         if (e != cudaSuccess) return e;
     }
 
     // stage 2: pair offsets in depth order, pair emission, passes over the tile half
     const long long n_groups = (long long)((vn + (size_t)kBlock * kReducePer - 1) / ((size_t)kBlock * kReducePer));
-    k_scan_reduce<<<(unsigned)n_groups, kBlock, 0, s>>>(p.proj->tiles, w.dvA, (long long)vn, w.tiles_sorted,
-                                                        w.chunk_sum, w.group_pre);
+    k_scan_reduce<<<(unsigned)n_groups, kBlock, 0, s>>>(p.proj->tiles, w.dvA, w.dvB, w.ctrl, (long long)vn,
+                                                        w.tiles_sorted, w.chunk_sum, w.group_pre);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n_groups <= 2 * kChunkScanThreads)
         k_chunk_scan<2><<<1, kChunkScanThreads, 0, s>>>(w.group_pre, n_groups, p.num_pairs);
@@ -687,7 +770,9 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
     DupArgs d;
     d.tiles_sorted = w.tiles_sorted;
     d.rect = reinterpret_cast<const int4 *>(p.proj->rect);
-    d.order = w.dvA;
+    d.order_a = w.dvA;
+    d.order_b = w.dvB;
+    d.plan = w.ctrl;
     d.chunk_sum = w.chunk_sum;
     d.group_pre = w.group_pre;
     d.vn = (long long)vn;
@@ -706,7 +791,7 @@ cudaError_t launch_bin(const BinLaunch &p, cudaStream_t s) {
         uint32_t *kout = even ? w.tkB : w.tkA;
         uint32_t *vout = last ? p.ids_out : (even ? w.tvB : w.tvA);
         e = radix_pass(even ? w.tkA : w.tkB, even ? w.tvA : w.tvB, kout, vout, last ? p.keys_out : nullptr,
-                       p.proj->depth, cnt_k, p.capacity, kRadixBits * pass, w, p.status, s);
+                       p.proj->depth, cnt_k, p.capacity, kRadixBits * pass, w, p.status, -1, s);
         if (e != cudaSuccess) return e;
     }
     const uint32_t *tiles_sorted = (tile_passes % 2) ? w.tkB : w.tkA;

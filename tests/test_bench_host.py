@@ -48,12 +48,29 @@ def test_launch_and_pass_accounting():
     # 1920x1080 in 16x16 tiles: 120 x 68 = 8160 tiles -> 13 bits -> 2 tile passes
     assert bench.tile_bits(8160) == 13
     assert bench.n_sort_passes(8160) == (4, 2)
+    assert bench.n_sort_passes(8160, 3) == (3, 2)
     assert bench.n_sort_passes(256) == (4, 1)
     assert bench.n_sort_passes(257) == (4, 2)
     # project 2 + binning (1 + 3*4 + 3 + 3*2 + 1) + fwd + bwd + project_bwd 2
     assert bench.launches_per_step(8160, persistent=False) == 29
     # + queue count and fill before each compositing kernel
     assert bench.launches_per_step(8160, persistent=True) == 33
+
+
+def test_depth_sort_passes():
+    """Passes over the depth keys: the drawn splats' key range (max - min + 1) in bits,
+    8 bits a pass; culled splats (tiles 0) do not widen it."""
+    import numpy as np
+    depths = np.array([5.82, 18.0, 7.5, 1e30, -3.0], np.float32)    # last two culled
+    tiles = np.array([3, 1, 2, 0, 0])
+    span = int(np.float32(18.0).view(np.uint32)) - int(np.float32(5.82).view(np.uint32)) + 1
+    assert span < 1 << 24
+    assert bench.depth_sort_passes(depths, tiles) == 3
+    assert bench.depth_sort_passes(np.array([1.0, 11.0], np.float32), np.array([1, 1])) == 4
+    assert bench.depth_sort_passes(np.array([2.0, 2.0], np.float32), np.array([1, 1])) == 1
+    assert bench.depth_sort_passes(depths, np.zeros(5, int)) == 0
+    # the byte count follows the passes
+    assert bench.alg_bytes(10, 0, 1, 4)["bin"] - bench.alg_bytes(10, 0, 1, 3)["bin"] == 10 * 20
 
 
 def test_algorithmic_bytes():

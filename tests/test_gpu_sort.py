@@ -50,3 +50,27 @@ def test_binning_many_partitions_bit_exact(cuda_ok, n, tile):
     assert np.array_equal(out["keys"], ref["keys"])
     assert np.array_equal(out["ids"], ref["ids"])
     assert np.array_equal(out["ranges"], ref["ranges"])
+
+
+@pytest.mark.parametrize("z0,z1,passes", [(4.0, 4.0, 1), (4.0, 4.003, 2), (4.0, 7.0, 3)])
+def test_depth_passes_follow_the_key_range(cuda_ok, z0, z1, passes):
+    """The depth stage sorts key - min in as many 8-bit passes as the drawn splats'
+    key range needs (all four are launched; the rest return at once).  Depths in
+    [z0, z1] on the optical-axis camera need `passes` passes; z0 = z1 gives equal keys,
+    whose order is the splat index alone.  Pairs and ranges bit-exact."""
+    import bench
+    rng = np.random.default_rng(91)
+    n = 50_001
+    sc = scenes.scene_uniform(rng, n, [-2.4, -1.4, z0], [2.4, 1.4, z1], -3.6, 0.5, 1.0, 1)
+    if z0 == z1:
+        sc.means[:, 2] = np.float32(z0)
+    cams = [scenes.identity_camera(640, 360, 500.0, 319.5, 179.5)]
+    pr = oracle.project(sc, cams[0], errmat=False)
+    assert bench.depth_sort_passes(pr["depth"], pr["tiles"]) == passes
+    ref = oracle.bin_pairs(pr, cams[0], (16, 16))
+    out = _gpu_bin(sc, cams, (16, 16), ref["n_pairs"] + 5000)
+    assert out["status"] == 0
+    assert out["keys"].size == ref["n_pairs"] > 4096 * 12
+    assert np.array_equal(out["keys"], ref["keys"])
+    assert np.array_equal(out["ids"], ref["ids"])
+    assert np.array_equal(out["ranges"], ref["ranges"])
