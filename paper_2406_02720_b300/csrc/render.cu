@@ -446,19 +446,30 @@ __device__ void bwd_produce(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
             const uint32_t slot = seq % NB;
             if (seq >= NB && !mbar_wait(&r.empty[slot], ((seq / NB) - 1) & 1u, p.status)) return;
             Batch<BATCH, true> &sb = r.buf[slot];
-            for (int k = lane; k < BATCH; k += 32) {
-                const uint32_t j = bstart + k;
-                if (j < bend) {
-                    uint32_t id = p.ids[j];
-                    if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
-                    stage<BATCH, true>(rec, id, sb, k, fox, foy, PLAIN);
-                }
-            }
             // the batch's visibility words (all bits set if the tile's rows had no room in
             // the mask: the warps then visit every entry, which changes no result)
             const int nw = (int)((bend - bstart + 31) >> 5) * NW;
             const size_t w0 = (vrow + ((bstart - ti.beg) >> 5)) * NW;
             for (int i = lane; i < nw; i += 32) r.vis[slot][i] = vfit ? __ldg(p.vis + w0 + i) : 0xffffffffu;
+            __syncwarp();
+            // lane q: the entries of chunk q that some pixel warp will visit
+            uint32_t any_w = 0;
+            if (lane < BATCH / 32 && lane * NW < nw) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) any_w |= r.vis[slot][lane * NW + w];
+            }
+            // only those are staged: no pixel warp reads the other slots
+#pragma unroll
+            for (int q = 0; q < BATCH / 32; ++q) {
+                const int k = lane + 32 * q;
+                const uint32_t j = bstart + k;
+                const uint32_t u = __shfl_sync(0xffffffffu, any_w, q);
+                if (j < bend && ((u >> lane) & 1u)) {
+                    uint32_t id = p.ids[j];
+                    if (id >= vn) { set_status(p.status, HGS_DEV_BOUNDS); id = 0; }
+                    stage<BATCH, true>(rec, id, sb, k, fox, foy, PLAIN);
+                }
+            }
             if (lane == 0) {
                 r.hdr[slot].gtile = gtile;
                 r.hdr[slot].bstart = bstart;
