@@ -57,10 +57,12 @@ typedef enum {
 } hgs_status;
 
 /* bits OR-ed into *dev_status by kernels */
-#define HGS_DEV_CAPACITY 0x1  /* more (tile, splat) pairs than pair_capacity     */
+#define HGS_DEV_CAPACITY 0x1  /* more (tile, splat) pairs than pair_capacity, or
+                                 a visibility mask too small for them           */
 #define HGS_DEV_TIMEOUT 0x2   /* a bounded wait between the warps of one block
-                                 (the backward compositing pipeline) ran past
-                                 its limit (1 s); the outputs are not meaningful */
+                                 (the forward and backward compositing
+                                 pipelines) ran past its limit (1 s); the
+                                 outputs are not meaningful                     */
 #define HGS_DEV_BOUNDS 0x4    /* an index was outside its array; access skipped  */
 
 /* Half-Gaussian parameters (Sec. 3.2), activated values, [n] rows; every array
@@ -277,7 +279,9 @@ hgs_status hgs_bin_static(const hgs_proj *proj, int n, const hgs_camera *cams_ho
  *                                composited at some pixel of block w.  Words of
  *                                chunks past every pixel's last composited entry
  *                                are left as they were.  A word beyond vis_words
- *                                is not written and sets HGS_DEV_CAPACITY.     */
+ *                                is not written and sets HGS_DEV_CAPACITY.
+ * Within a block, one warp stages each tile's list in batches and the others walk
+ * them, synchronised by bounded waits: HGS_DEV_TIMEOUT if one runs out. */
 hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
                           const uint32_t *ranges, const hgs_camera *cams_host,
                           const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
@@ -359,8 +363,8 @@ hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, co
 hgs_status hgs_probe_peak(int kind, int blocks_per_sm, int iters, float *sink, double *lane_ops,
                           void *stream);
 
-/* Self-test of the bounded wait of the backward compositing pipeline
- * (hgs_rasterize_bwd; the paper has no counterpart).  One warp waits on a shared-memory mbarrier that nothing completes;
+/* Self-test of the bounded wait of the compositing pipelines (hgs_render_fwd,
+ * hgs_rasterize_bwd; the paper has no counterpart).  One warp waits on a shared-memory mbarrier that nothing completes;
  * the wait ends at its bound (about 1 s), HGS_DEV_TIMEOUT is OR-ed into
  * *dev_status and the kernel returns, so the device stays usable.  HGS_ERR_INVALID
  * if dev_status is NULL (nothing enqueued). */
