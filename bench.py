@@ -129,11 +129,53 @@ def _scene(args):
     return _SCENE[args.n]
 
 
+def _phase_step_class():
+    from paper_2406_02720_b300.rasterizer import GraphStep
+
+    class PhaseStep(GraphStep):
+        """The fwd+bwd step with an event recorded (as an external graph node) between
+        its phases, for the per-phase breakdown; mean ms per phase over replays, each
+        replay synchronised."""
+        names = ("project", "bin", "render_fwd", "render_bwd", "project_bwd")
+
+        def __init__(self, *a, **kw):
+            import torch
+            self.evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(self.names) + 1)]
+            super().__init__(*a, **kw)
+
+        def _body(self, backward):
+            r, evs = self.rast, self.evs
+            r.status.zero_()
+            evs[0].record()
+            r.project(self.g)
+            evs[1].record()
+            r.bin()
+            evs[2].record()
+            r.render_fwd()
+            evs[3].record()
+            r.rasterize_bwd(self.dL)
+            evs[4].record()
+            r.project_bwd(self.g, self.grads)
+            evs[5].record()
+
+        def phase_ms(self, replays):
+            ph = {k: [] for k in self.names}
+            for _ in range(replays):
+                self.replay()
+                self.evs[-1].synchronize()
+                for k, nm in enumerate(self.names):
+                    ph[nm].append(self.evs[k].elapsed_time(self.evs[k + 1]))
+            return {k: statistics.mean(v) for k, v in ph.items()}
+
+    return PhaseStep
+
+
 def run_gpu(args):
     import torch
     from paper_2406_02720_b300 import hgs as H
     from paper_2406_02720_b300.rasterizer import Gaussians, GraphStep, Rasterizer
 
+    PhaseStep = _phase_step_class()
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist_mod = init_dist(ws, "nccl")
@@ -150,29 +192,9 @@ def run_gpu(args):
     dL = torch.from_numpy(dL_np.reshape(-1)).to(dev)
     grads = Gaussians.empty_like(g)
 
-    # phase events recorded inside the graph (external nodes)
-    names = ["project", "bin", "render_fwd", "render_bwd", "project_bwd"]
-    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(names) + 1)]
-
-    class Step(GraphStep):
-        def _body(self, backward):
-            r = self.rast
-            r.status.zero_()
-            evs[0].record()
-            r.project(self.g)
-            evs[1].record()
-            r.bin()
-            evs[2].record()
-            r.render_fwd()
-            evs[3].record()
-            r.rasterize_bwd(self.dL)
-            evs[4].record()
-            r.project_bwd(self.g, self.grads)
-            evs[5].record()
-
     # the timed step: the plain graph (the phase events of `step` cost ~10 us per replay,
     # ~0.1 ms in the pipelined end-to-end loop); `step` only for the phase breakdown
-    step = Step(rast, g, dL, grads)
+    step = PhaseStep(rast, g, dL, grads)
     plain_step = GraphStep(rast, g, dL, grads)
     torch.cuda.synchronize()
     st = rast.read_status()
@@ -205,13 +227,7 @@ def run_gpu(args):
         raise RuntimeError(f"device status {st} in timed region")
 
     # ---- per-phase times from the in-graph events (K more replays, synced each) ---------
-    ph = {k: [] for k in names}
-    for _ in range(args.steps):
-        step.replay()
-        evs[-1].synchronize()
-        for k, nm in enumerate(names):
-            ph[nm].append(evs[k].elapsed_time(evs[k + 1]))
-    phases = {k: statistics.mean(v) for k, v in ph.items()}
+    phases = step.phase_ms(args.steps)
 
     # ---- forward-only step -------------------------------------------------------------------
     fwd_step = GraphStep(rast, g, dL, grads, backward=False)
@@ -266,7 +282,7 @@ def run_gpu(args):
         result["rect_mode_2"] = run_rect_mode(args, dev, g, dL, rast, n_pairs, 2)
         result["mip"] = run_mip(args, dev, g, dL, rast)
     if args.sweep:
-        result["sweep"] = run_sweep(args, dev)
+        result["sweep"] = run_sweep(args, dev, alu=alu)
     if args.multiview:
         del step, fwd_step
         torch.cuda.empty_cache()
@@ -674,14 +690,19 @@ def run_sharded(args, dev, dist_mod):
 
 
 # ---- stress sweep (disks with grazing planes, 100k..6M splats) --------------------------------
-def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_000)):
+def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_000), alu=None):
     """fwd+bwd throughput curve over the splat count at 1920x1080, 30% 100:1 disks
-    with splitting planes within 5 degrees of the ray, plus the equal-opacity copy."""
+    with splitting planes within 5 degrees of the ray, plus the equal-opacity copy.
+    Each point also carries its per-phase times (events inside a second graph of the
+    step) and each phase's roofline fraction: HBM for projection, binning and the
+    projection adjoint (algorithmic bytes), FP32 / MUFU for the two compositing
+    kernels (counted events x ops per event)."""
     import torch
     from paper_2406_02720_b300 import hgs as H
     from paper_2406_02720_b300 import scenes
     from paper_2406_02720_b300.multiview import time_replays
     from paper_2406_02720_b300.rasterizer import Gaussians, GraphStep, Rasterizer
+    PhaseStep = _phase_step_class()
     out = []
     runs = [(n, False) for n in sizes] + [(3_000_000, True)]
     for n, equal in runs:
@@ -692,14 +713,21 @@ def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_00
                                               persistent=args.persistent), device=dev)
         r.forward(g)
         r._alloc_pairs(int(r.num_pairs.item() * 1.05) + 4096)
+        n_pairs = int(r.num_pairs.item())
         grads = Gaussians.empty_like(g)
         step = GraphStep(r, g, dL, grads)
         ms = time_replays(step, args.sweep_steps)
         st = r.read_status()
+        pstep = PhaseStep(r, g, dL, grads)
+        phases = pstep.phase_ms(max(3, args.sweep_steps // 2))
+        st |= r.read_status()
+        stats = r.stats(dL)
+        dpasses = depth_sort_passes(r.depth.cpu().numpy(), r.tiles.cpu().numpy())
         pix = cams[0].width * cams[0].height
         out.append({"n": n, "equal_opacity": equal, "ms_per_step": ms, "Mpixel_per_s": pix / (ms * 1e3),
-                    "pairs": int(r.num_pairs.item()), "status": st})
-        del step, r, g, grads
+                    "pairs": n_pairs, "status": st, "phases_ms": phases, "depth_sort_passes": dpasses,
+                    "phase_roofline": phase_rooflines(phases, stats, n_pairs, n, r.total_tiles, alu, dpasses)})
+        del step, pstep, r, g, grads
         torch.cuda.empty_cache()
     return out
 
