@@ -377,6 +377,18 @@ def alu_work(stats, key):
     return fp32, mufu
 
 
+def bwd_atomics(stats, render_bwd_ms):
+    """The backward's gradient atomics (counter bwd_atomic): lanes that added their 12
+    gradients to the per-splat rows, three 16-byte vector reductions each, against one
+    such lane per contributing pair without the in-warp folds; and their rate over the
+    compositing backward's time."""
+    n, c = stats.get("bwd_atomic", 0), stats["bwd_contrib"]
+    t = render_bwd_ms * 1e-3
+    return {"lane_atomics": n, "vector_reductions": 3 * n, "float_adds": 12 * n,
+            "float_adds_unfolded": 12 * c, "pairs_per_lane_atomic": c / n if n else None,
+            "G_float_adds_per_s": 12 * n / t / 1e9, "GB_reduced_per_s": 48 * n / t / 1e9}
+
+
 # DRAM bytes per launch of a kernel, from its committed ncu summary, valid only while
 # the kernel source is the one the summary was captured from (sha256 recorded there).
 PROFILE_OF = {"render_bwd": ("profiles/ncu_render_bwd_3M_1080p.md", "paper_2406_02720_b300/csrc/render.cu"),
@@ -471,6 +483,8 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None, dept
                         "frac": f_mufu})
         out.update({"traffic": profiled_traffic(dom), "frac_fp32": f_fp32, "frac_mufu": f_mufu,
                     "note": f"peak {peak_src}; algorithmic ops = counted events x ops per event"})
+        if dom == "render_bwd":
+            out["atomics"] = bwd_atomics(stats, phases[dom])
     else:
         b = alg_bytes(n, n_pairs, total_tiles, depth_passes).get(dom, 0)
         ach = b / (phases[dom] * 1e-3) / 1e9
@@ -493,6 +507,7 @@ def phase_rooflines(phases, stats, n_pairs, n, total_tiles, measured=None, depth
         t = phases[ph] * 1e-3
         out[ph] = {"bound": "alu", "frac_fp32": fp32 / t / (fp32_peak * 1e12),
                    "frac_mufu": mufu / t / (mufu_peak * 1e12)}
+    out["render_bwd"]["atomics"] = bwd_atomics(stats, phases["render_bwd"])
     return out
 
 

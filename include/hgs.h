@@ -343,7 +343,9 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
  *   3-sigma/opacity cut-off)  [2] splats composited  [3] backward iterations
  *   [4] backward full evaluations  [5] backward contributing pairs
  *   [6] backward (warp, splat) visits with more than 12 contributing lanes (folded
- *   by one shuffle level before the atomics)  [7] reserved (0). */
+ *   by shuffles before the atomics: lane l + 16 into lane l, and above 16 lanes
+ *   also l + 8 into l)  [7] backward gradient atomics: lanes that added their 12
+ *   gradients to grad2d (three 16-byte vector reductions each), at most [5]. */
 hgs_status hgs_render_stats(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                             const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                             const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,

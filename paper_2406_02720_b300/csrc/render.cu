@@ -491,7 +491,7 @@ __device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr bool plain = PLAIN;
     float *grad = p.grad2d;
-    unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0;
+    unsigned long long c_visit = 0, c_full = 0, c_contrib = 0, c_red = 0, c_atom = 0;
     // per-tile state of this lane's pixel
     bool inside = false;
     f32x2 fp = 0;
@@ -603,7 +603,10 @@ __device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
                 if (!any) continue;
                 float *dst = grad + 12 * (size_t)s.id[k];
                 if (__popc(any) <= kFoldAbove) {
-                    if (contrib) atomic_add12(dst, gr);
+                    if (contrib) {
+                        atomic_add12(dst, gr);
+                        if (COUNT) ++c_atom;
+                    }
                 } else {
                     if (COUNT && lane == 0) ++c_red;
                     // lane l + 16 into lane l, two gradients per paired addition
@@ -621,9 +624,13 @@ __device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
                                                   __shfl_xor_sync(0xffffffffu, gr[f + 1], 8));
                             unpack2(add2(pack2(gr[f], gr[f + 1]), o), gr[f], gr[f + 1]);
                         }
-                        if (lane < 8 && ((any >> lane) & 0x01010101u)) atomic_add12(dst, gr);
+                        if (lane < 8 && ((any >> lane) & 0x01010101u)) {
+                            atomic_add12(dst, gr);
+                            if (COUNT) ++c_atom;
+                        }
                     } else if (lane < 16 && ((any >> lane) & 0x10001u)) {
                         atomic_add12(dst, gr);
+                        if (COUNT) ++c_atom;
                     }
                 }
             }
@@ -631,7 +638,11 @@ __device__ void bwd_consume(const RenderLaunch &p, BwdRing<BATCH, TW * TH / 32> 
         __syncwarp();
         if (lane == 0) mbar_arrive(&r.empty[slot]);
     }
-    if (COUNT) add_counters(p.counters + 3, c_visit, c_full, c_contrib, c_red);
+    if (COUNT) {
+        add_counters(p.counters + 3, c_visit, c_full, c_contrib, c_red);
+        c_atom = warp_sum_u64(c_atom);
+        if (lane == 0 && c_atom) atomicAdd(p.counters + 7, c_atom);
+    }
 }
 
 // ---- forward -------------------------------------------------------------------------

@@ -223,7 +223,8 @@ def hgs_selftest_wait(dev_status, stream):
     _check(lib().hgs_selftest_wait(dev_status, stream), "hgs_selftest_wait")
 
 
-STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd_contrib", "bwd_warp_red"]
+STAT_NAMES = ["fwd_visit", "fwd_full", "fwd_comp", "bwd_visit", "bwd_full", "bwd_contrib", "bwd_warp_red",
+              "bwd_atomic"]
 
 
 # ---- struct builders ----------------------------------------------------------------------

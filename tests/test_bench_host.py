@@ -124,3 +124,13 @@ def test_profiled_traffic_needs_the_profiled_source(tmp_path, monkeypatch):
     src.write_text("kernel v2")                      # the kernel changed since the capture
     assert bench.profiled_traffic("render_bwd") is None
     assert bench.profiled_traffic("bin") is None
+
+
+def test_backward_atomics_report():
+    import bench
+    stats = {"bwd_contrib": 1000, "bwd_atomic": 250}
+    a = bench.bwd_atomics(stats, 0.5)
+    assert a["vector_reductions"] == 750 and a["float_adds"] == 3000 and a["float_adds_unfolded"] == 12000
+    assert a["pairs_per_lane_atomic"] == 4.0
+    assert abs(a["G_float_adds_per_s"] - 3000 / 0.5e-3 / 1e9) < 1e-12
+    assert abs(a["GB_reduced_per_s"] - 4 * a["G_float_adds_per_s"]) < 1e-12
