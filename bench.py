@@ -516,27 +516,38 @@ def run_e2e(args, rast, g, dL, grads, pixels, dev):
     PCIe inside the timed region.  The splat parameters are the model's state and stay
     resident in HBM (as weights do in a training step); each step's inputs are its
     camera and the upstream image gradient dL/dimage, copied from pinned host memory,
-    and its result is the rendered image, copied back to pinned host memory.  PCIe
-    copies run on two side streams, double-buffered, so step k+1's upload and step k's
-    download overlap step k's kernels.  Each staging buffer has its own graph of the
-    step, which reads dL/dimage from it directly and copies the camera in and the image
-    out on the device, so each step is one graph launch.  (Capturing the copies as
-    graph branches parallel to the kernels measured no faster.)"""
+    and its result is the rendered image, copied back to pinned host memory.  The
+    copies run on two side streams, double-buffered: each staging buffer has its own
+    graph of the step, which reads dL/dimage from it, copies the camera in on the
+    device and composites the image straight into its image buffer, so each step is
+    one graph launch.  Both copies start when step k's forward compositing ends (an
+    event recorded inside the graph): step k's image is final then, and the upload
+    of step k+1's inputs lands while step k's backward runs.  The backward is
+    issue-bound and leaves the L2 alone; copies started with the step instead land
+    during the binning, whose depth passes run from L2, and cost 40 us more per step
+    (2.806 against 2.847 ms on the 3M / 1080p step)."""
     import torch
     from paper_2406_02720_b300.rasterizer import GraphStep
 
     class StagedStep(GraphStep):
-        """The step reading dL/dimage straight from its staging buffer (one graph per
-        buffer), with the camera copied in and the image copied out inside the graph."""
+        """The step reading dL/dimage and the camera from its staging buffers and
+        compositing into its own image buffer; `fwd_done` is recorded in the graph
+        when the forward compositing ends."""
 
         def __init__(self, src_dl, src_cam, dst_img):
             self.src_cam, self.dst_img = src_cam, dst_img
+            self.fwd_done = torch.cuda.Event(external=True)
             super().__init__(rast, g, src_dl, grads)
 
         def _body(self, backward):
-            self.rast.cams_dev.copy_(self.src_cam, non_blocking=True)
-            super()._body(backward)
-            self.dst_img.copy_(self.rast.image, non_blocking=True)
+            r = self.rast
+            r.cams_dev.copy_(self.src_cam, non_blocking=True)
+            r.status.zero_()
+            r.project(self.g)
+            r.bin()
+            r.render_fwd(self.dst_img)
+            self.fwd_done.record()
+            r.backward_async(self.g, self.dL, self.grads)
 
     main = torch.cuda.current_stream(dev)
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -548,36 +559,35 @@ def run_e2e(args, rast, g, dL, grads, pixels, dev):
     stage_cam = [rast.cams_dev.detach().clone() for _ in range(2)]
     stage_img = [torch.empty_like(rast.image) for _ in range(2)]
     steps = [StagedStep(stage_dl[b], stage_cam[b], stage_img[b]) for b in range(2)]
-    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "free_in", "done", "free_out")}
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_free_out = [torch.cuda.Event() for _ in range(2)]
     h2d = dL.numel() * dL.element_size() + cam_bytes
     d2h = rast.image.numel() * rast.image.element_size()
 
-    def upload(k):
+    def upload(k, after=None):
+        # staging buffer k % 2 was last read by step k - 2, which ended before step k - 1
+        # (the trigger's step) began
         b = k % 2
-        s_in.wait_event(ev["free_in"][b])
+        if after is not None:
+            s_in.wait_event(after)
         with torch.cuda.stream(s_in):
             stage_dl[b].copy_(host_dl[b], non_blocking=True)
             stage_cam[b].copy_(host_cam[b], non_blocking=True)
-        ev["in"][b].record(s_in)
-
-    def compute_and_download(k):
-        b = k % 2
-        main.wait_event(ev["in"][b])
-        main.wait_event(ev["free_out"][b])
-        steps[b].replay()
-        ev["free_in"][b].record(main)
-        ev["done"][b].record(main)
-        s_out.wait_event(ev["done"][b])
-        with torch.cuda.stream(s_out):
-            host_img[b].copy_(stage_img[b], non_blocking=True)
-        ev["free_out"][b].record(s_out)
+        ev_in[b].record(s_in)
 
     def run(k_steps):
         upload(0)
         for k in range(k_steps):
+            b = k % 2
+            main.wait_event(ev_in[b])          # this step's inputs are on the device
+            main.wait_event(ev_free_out[b])    # step k - 2's image has left its buffer
+            steps[b].replay()
             if k + 1 < k_steps:
-                upload(k + 1)
-            compute_and_download(k)
+                upload(k + 1, steps[b].fwd_done)
+            s_out.wait_event(steps[b].fwd_done)
+            with torch.cuda.stream(s_out):
+                host_img[b].copy_(stage_img[b], non_blocking=True)
+            ev_free_out[b].record(s_out)
         main.wait_stream(s_out)
 
     run(3)
@@ -591,12 +601,14 @@ def run_e2e(args, rast, g, dL, grads, pixels, dev):
     torch.cuda.synchronize()
     if rast.read_status():
         raise RuntimeError("device status during the end-to-end run")
+    if not torch.equal(host_img[(k - 1) % 2].to(dev), rast.image):
+        raise RuntimeError("the image read back is not the step's image")
     ms = e0.elapsed_time(e1) / k
     del steps
     return {"value": pixels / (ms * 1e3), "unit": "Mpixel/s", "ms_per_step": ms,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "note": "per step: camera + dL/dimage host->device, image device->host (pinned, overlapped "
-                    "with compute); splat parameters and gradients resident in HBM"}
+                    "with the backward); splat parameters and gradients resident in HBM"}
 
 
 def run_e2e_params_over_pcie(args, rast, g, dL, grads, step, pixels, dev):

@@ -134,10 +134,17 @@ class Rasterizer:
                   self.bin_ws.numel(), self.capacity, _vp(self.keys), _vp(self.ids), _vp(self.ranges),
                   _vp(self.num_pairs), _vp(self.status), self._stream())
 
-    def render_fwd(self):
+    def render_fwd(self, image: torch.Tensor = None):
+        """Composites into self.image, or into `image` (same size and dtype) when given,
+        e.g. a staging buffer that a copy to the host reads next."""
+        if image is None:
+            image = self.image
+        elif (image.numel() != self.image.numel() or image.dtype != self.image.dtype
+              or image.device != self.image.device or not image.is_contiguous()):
+            raise ValueError("image buffer must match the rasterizer's image (size, dtype, device, contiguous)")
         H.hgs_render_fwd(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                          _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
-                         _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
+                         _vp(image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
                          _vp(self.status), self._stream())
 
     def rasterize_bwd(self, dL_dimage: torch.Tensor):

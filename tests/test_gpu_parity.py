@@ -244,3 +244,20 @@ def test_empty_and_all_culled(cuda_ok):
     out = gpu_render(one, cams)
     ref = oracle.render(one, cams[0])
     compare_image(out["images"][0], out["T"][0], out["n_contrib"][0], ref, label="one splat")
+
+
+def test_forward_into_a_caller_buffer(cuda_ok):
+    """render_fwd(image=buf) composites the same image into buf (the end-to-end path
+    renders straight into its staging buffer); a buffer of another size is refused on
+    the host before anything is enqueued."""
+    import torch
+    sc, cams = scenes.config1()
+    out = gpu_render(sc, cams)
+    r = out["rast"]
+    buf = torch.full_like(r.image, -1.0)
+    r.clear_status()
+    r.render_fwd(buf)
+    assert r.read_status() == 0
+    assert torch.equal(buf, r.image)
+    with pytest.raises(ValueError):
+        r.render_fwd(torch.empty(r.image.numel() - 1, device=r.image.device))
