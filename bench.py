@@ -247,7 +247,8 @@ def run_gpu(args):
     stats = rast.stats(dL)
     alu = measure_alu_peaks(dev)
     dpasses = depth_sort_passes(rast.depth.cpu().numpy(), rast.tiles.cpu().numpy())
-    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks, alu, dpasses)
+    drawn = int((rast.tiles > 0).sum().item())
+    roof = roofline(phases, stats, n_pairs, sc.n, rast.total_tiles, clocks, alu, dpasses, drawn)
 
     # ---- end to end through host buffers --------------------------------------------------
     e2e = run_e2e(args, rast, g, dL, grads, pixels, dev)
@@ -271,8 +272,8 @@ def run_gpu(args):
                                    "all-reduce in 'sharded'"),
                    "l2": "inputs larger than L2 (756 MB of parameters read per step)"},
         "fwd_ms": fwd_ms, "phases_ms": phases, "work": stats, "roofline": roof,
-        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles, alu, dpasses),
-        "depth_sort_passes": dpasses,
+        "phase_roofline": phase_rooflines(phases, stats, n_pairs, sc.n, rast.total_tiles, alu, dpasses, drawn=drawn),
+        "depth_sort_passes": dpasses, "drawn_splats": drawn,
         "alu_peaks": alu,
         "clocks": clocks,
         "e2e": e2e, "e2e_params_over_pcie": e2e_full, "gpu_launches": launches * args.steps,
@@ -286,7 +287,7 @@ def run_gpu(args):
     if args.multiview:
         del step, fwd_step
         torch.cuda.empty_cache()
-        result["multiview"] = run_multiview(args, dev)
+        result["multiview"] = run_multiview(args, dev, alu=alu)
     if dist_mod is not None:
         torch.cuda.empty_cache()
         result["sharded"] = run_sharded(args, dev, dist_mod)
@@ -334,24 +335,30 @@ def launches_per_step(total_tiles, persistent=False):
     return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + 2 * (3 if persistent else 1) + 2
 
 
-def alg_bytes(n, n_pairs, total_tiles, depth_passes=4):
-    """Bytes each memory-bound phase must move in this design (per launch sequence):
-      project     : 252 B parameters read (mean 12, scale 12, quat 16, normal 12,
-                    opacities 8, SH 192) + 88 B written (record 64, depth 4, rect 16,
-                    tiles 4) per splat
-      bin         : per splat: depth keys 16 (read depth+tiles, write key+id), one to
+def alg_bytes(n, n_pairs, total_tiles, depth_passes=4, views=1, drawn=None):
+    """Bytes each memory-bound phase must move in this design (per launch sequence),
+    for n splats seen by `views` cameras (n * views (view, splat) entries), `drawn` of
+    the entries drawn (all when None):
+      project     : 252 B parameters read per splat (mean 12, scale 12, quat 16,
+                    normal 12, opacities 8, SH 192), read once for all views; per entry
+                    24 B written (depth 4, rect 16, tiles 4), and the 64 B record per
+                    drawn entry
+      bin         : per entry: depth keys 16 (read depth+tiles, write key+id), one to
                     four depth passes (as the keys' range needs) x 20 (upsweep reads 4,
                     downsweep reads 8 writes 8), scan 12
                     (read order + tiles, write tiles in depth order), duplicate 24
                     (order, tiles in depth order, rect);
                     per pair: 8 written by duplicate, 20 per tile pass, 4 read by ranges;
                     8 per tile written by ranges
-      project_bwd : 252 B parameters + 48 B screen-space gradients read, 252 B written
+      project_bwd : 252 B parameters read and 252 B gradients written per splat, 48 B
+                    screen-space gradients read per entry
     """
     dp, tp = n_sort_passes(total_tiles, depth_passes)
-    return {"project": n * (252 + 88),
-            "bin": n * (16 + 20 * dp + 12 + 24) + n_pairs * (8 + 20 * tp + 4) + total_tiles * 8,
-            "project_bwd": n * (252 + 48 + 252)}
+    e = n * views
+    d = e if drawn is None else drawn
+    return {"project": n * 252 + e * 24 + d * 64,
+            "bin": e * (16 + 20 * dp + 12 + 24) + n_pairs * (8 + 20 * tp + 4) + total_tiles * 8,
+            "project_bwd": n * (252 + 252) + e * 48}
 
 
 # Algorithmic operations per counted event of the compositing kernels, counted
@@ -461,7 +468,7 @@ def alu_peaks(measured):
             f"computed: 148 SMs x (128 FP32 | 16 MUFU) lanes x {mhz:.0f} MHz")
 
 
-def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None, depth_passes=4):
+def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None, depth_passes=4, drawn=None):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     src = "of measured" if hbm else "of fallback"
@@ -486,20 +493,20 @@ def roofline(phases, stats, n_pairs, n, total_tiles, clocks, measured=None, dept
         if dom == "render_bwd":
             out["atomics"] = bwd_atomics(stats, phases[dom])
     else:
-        b = alg_bytes(n, n_pairs, total_tiles, depth_passes).get(dom, 0)
+        b = alg_bytes(n, n_pairs, total_tiles, depth_passes, drawn=drawn).get(dom, 0)
         ach = b / (phases[dom] * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": None, "note": src})
     return out
 
 
-def phase_rooflines(phases, stats, n_pairs, n, total_tiles, measured=None, depth_passes=4):
+def phase_rooflines(phases, stats, n_pairs, n, total_tiles, measured=None, depth_passes=4, views=1, drawn=None):
     """HBM fraction of the memory-bound phases and ALU fractions of the compositing
     phases (each against its own bound; algorithmic bytes/ops per launch)."""
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6400.0)
     out = {}
-    for k, b in alg_bytes(n, n_pairs, total_tiles, depth_passes).items():
+    for k, b in alg_bytes(n, n_pairs, total_tiles, depth_passes, views, drawn).items():
         out[k] = {"bound": "hbm", "GBs": b / (phases[k] * 1e-3) / 1e9, "frac": b / (phases[k] * 1e-3) / 1e9 / hbm}
     fp32_peak, mufu_peak, _ = alu_peaks(measured)
     for key, ph in (("fwd", "render_fwd"), ("bwd", "render_bwd")):
@@ -646,10 +653,12 @@ def run_e2e_params_over_pcie(args, rast, g, dL, grads, step, pixels, dev):
 
 
 # ---- batched multi-view vs one launch sequence per view ----------------------------------------
-def run_multiview(args, dev):
+def run_multiview(args, dev, alu=None):
     """64 cameras of uneven size over a 1M-splat scene: views/s of the batched
     persistent path against the per-view path, both CUDA-graph captured, same
-    tile shape (autotuned for the batched path) and the same images."""
+    tile shape (autotuned for the batched path) and the same images; plus the
+    batched step's phase times (events inside a second graph of it) and each phase's
+    roofline fraction."""
     import torch
     from paper_2406_02720_b300 import autotune, scenes
     from paper_2406_02720_b300.multiview import BatchedStep, PerViewStep, packed_upstream, time_replays
@@ -665,7 +674,15 @@ def run_multiview(args, dev):
     st_b = b.status()
     imgs_b = [x.clone() for x in b.images()]
     pairs = int(b.rast.num_pairs.item())
-    del b
+    pstep = _phase_step_class()(b.rast, g, dLp, b.grads)
+    phases = pstep.phase_ms(5)
+    st_b |= b.status()
+    stats = b.rast.stats(dLp)
+    dpasses = depth_sort_passes(b.rast.depth.cpu().numpy(), b.rast.tiles.cpu().numpy())
+    drawn = int((b.rast.tiles > 0).sum().item())
+    proof = phase_rooflines(phases, stats, pairs, sc.n, b.rast.total_tiles, alu, dpasses, views=len(cams),
+                            drawn=drawn)
+    del pstep, b
     torch.cuda.empty_cache()
     p = PerViewStep(cams, g, dL, tile=tile, batch=batch, device=dev)
     ms_p = time_replays(p, args.mv_steps)
@@ -681,7 +698,9 @@ def run_multiview(args, dev):
             "autotune_ms": timings, "batched_ms_per_step": ms_b, "per_view_ms_per_step": ms_p,
             "batched_views_per_s": V / (ms_b * 1e-3), "per_view_views_per_s": V / (ms_p * 1e-3),
             "speedup": ms_p / ms_b, "batched_Mpixel_per_s": pix / (ms_b * 1e3),
-            "images_identical": same, "status": st_b | st_p, "steps": args.mv_steps}
+            "images_identical": same, "status": st_b | st_p, "steps": args.mv_steps,
+            "batched_phases_ms": phases, "batched_work": stats, "batched_depth_sort_passes": dpasses,
+            "batched_drawn_entries": drawn, "batched_phase_roofline": proof}
 
 
 def run_sharded(args, dev, dist_mod):
@@ -750,10 +769,13 @@ def run_sweep(args, dev, sizes=(100_000, 500_000, 1_000_000, 3_000_000, 6_000_00
         st |= r.read_status()
         stats = r.stats(dL)
         dpasses = depth_sort_passes(r.depth.cpu().numpy(), r.tiles.cpu().numpy())
+        drawn = int((r.tiles > 0).sum().item())
         pix = cams[0].width * cams[0].height
         out.append({"n": n, "equal_opacity": equal, "ms_per_step": ms, "Mpixel_per_s": pix / (ms * 1e3),
                     "pairs": n_pairs, "status": st, "phases_ms": phases, "depth_sort_passes": dpasses,
-                    "phase_roofline": phase_rooflines(phases, stats, n_pairs, n, r.total_tiles, alu, dpasses)})
+                    "drawn_splats": drawn,
+                    "phase_roofline": phase_rooflines(phases, stats, n_pairs, n, r.total_tiles, alu, dpasses,
+                                                      drawn=drawn)})
         del step, pstep, r, g, grads
         torch.cuda.empty_cache()
     return out

@@ -78,6 +78,12 @@ def test_algorithmic_bytes():
     assert b["project"] == 1000 * 340
     assert b["project_bwd"] == 1000 * 552
     assert b["bin"] == 1000 * (16 + 80 + 12 + 24) + 5000 * (8 + 40 + 4) + 8160 * 8
+    # 64 views, 40k of the 64k (view, splat) entries drawn: parameters read once, entry
+    # fields per entry, records per drawn entry; 308,780 tiles take three tile passes
+    m = bench.alg_bytes(1000, 5000, 308780, depth_passes=3, views=64, drawn=40000)
+    assert m["project"] == 1000 * 252 + 64000 * 24 + 40000 * 64
+    assert m["project_bwd"] == 1000 * 504 + 64000 * 48
+    assert m["bin"] == 64000 * (16 + 60 + 12 + 24) + 5000 * (8 + 60 + 4) + 308780 * 8
 
 
 def test_clock_summary():
