@@ -205,6 +205,9 @@ static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids
     p->n_contrib = nullptr;
     p->vis = nullptr;
     p->vis_words = 0;
+    p->clear = nullptr;
+    p->clear_n4 = 0;
+    p->grad2d_cleared = false;
     p->dL_dimage = nullptr;
     p->grad2d = nullptr;
     p->status = nullptr;
@@ -215,11 +218,17 @@ static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids
 hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids, const uint32_t *ranges,
                           const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                           const hgs_config *cfg, void *ws, size_t ws_bytes, float *image, float *final_T,
-                          uint32_t *n_contrib, uint32_t *vis, size_t vis_words, int *dev_status, void *stream) {
+                          uint32_t *n_contrib, uint32_t *vis, size_t vis_words, float *grad2d_clear,
+                          int *dev_status, void *stream) {
     RenderLaunch p;
     hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
     if (st != HGS_OK) return st;
-    if (!image || !final_T || !n_contrib || !vis) return HGS_ERR_INVALID;
+    if (!image || !final_T || !n_contrib || !vis || (grad2d_clear && !aligned16(grad2d_clear)))
+        return HGS_ERR_INVALID;
+    if (grad2d_clear) {
+        p.clear = reinterpret_cast<float4 *>(grad2d_clear);
+        p.clear_n4 = 3 * (size_t)n * (size_t)n_views;      // 12 floats per (view, splat)
+    }
     p.image = image;
     p.final_T = final_T;
     p.n_contrib = n_contrib;
@@ -233,7 +242,8 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, c
                              const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                              const hgs_config *cfg, void *ws, size_t ws_bytes, const float *final_T,
                              const uint32_t *n_contrib, const uint32_t *vis, size_t vis_words,
-                             const float *dL_dimage, float *grad2d, int *dev_status, void *stream) {
+                             const float *dL_dimage, float *grad2d, int grad2d_cleared, int *dev_status,
+                             void *stream) {
     RenderLaunch p;
     hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
     if (st != HGS_OK) return st;
@@ -245,6 +255,7 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, c
     p.vis_words = vis_words;
     p.dL_dimage = dL_dimage;
     p.grad2d = grad2d;
+    p.grad2d_cleared = grad2d_cleared != 0;
     p.status = dev_status;
     return cuda_status(launch_render_bwd(p, static_cast<cudaStream_t>(stream)));
 }
@@ -306,7 +317,7 @@ hgs_status hgs_render_bwd(const hgs_gaussians *g, const hgs_proj *proj, const ui
                           const hgs_gaussian_grads *out, int *dev_status, void *stream) {
     if (!g) return HGS_ERR_INVALID;
     hgs_status st = hgs_rasterize_bwd(proj, g->n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes,
-                                      final_T, n_contrib, vis, vis_words, dL_dimage, grad2d, dev_status, stream);
+                                      final_T, n_contrib, vis, vis_words, dL_dimage, grad2d, 0, dev_status, stream);
     if (st != HGS_OK) return st;
     return hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, proj->fp64_list, dev_status, stream);
 }

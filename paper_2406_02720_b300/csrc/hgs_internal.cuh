@@ -107,6 +107,9 @@ struct RenderLaunch {
     uint32_t *n_contrib;
     uint32_t *vis;                  // visibility mask (forward output, backward input)
     size_t vis_words;
+    float4 *clear;                  // forward: zeroed by the kernel (the backward's grad2d), or null
+    size_t clear_n4;                // its length in float4
+    bool grad2d_cleared;            // backward: grad2d is already zero (no clearing)
     // backward
     const float *dL_dimage;
     float *grad2d;

@@ -90,10 +90,10 @@ def lib():
                                      vp]
         L.hgs_render_fwd.restype = c_int
         L.hgs_render_fwd.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp,
-                                     c_size_t, vp, vp, vp, vp, c_size_t, vp, vp]
+                                     c_size_t, vp, vp, vp, vp, c_size_t, vp, vp, vp]
         L.hgs_rasterize_bwd.restype = c_int
         L.hgs_rasterize_bwd.argtypes = [POINTER(HgsProj), c_int, vp, vp, _CAM_P, vp, c_int, _CFG_P, vp,
-                                        c_size_t, vp, vp, vp, c_size_t, vp, vp, vp, vp]
+                                        c_size_t, vp, vp, vp, c_size_t, vp, vp, c_int, vp, vp]
         L.hgs_project_bwd.restype = c_int
         L.hgs_project_bwd.argtypes = [POINTER(HgsGaussians), _CAM_P, vp, c_int, _CFG_P, vp,
                                       POINTER(HgsGaussianGrads), vp, vp, vp]
@@ -177,17 +177,17 @@ def hgs_bin_static(proj, n, cams_host, n_views, cfg, pair_capacity, keys_out, id
 
 
 def hgs_render_fwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, image, final_T,
-                   n_contrib, vis, vis_words, dev_status, stream):
+                   n_contrib, vis, vis_words, grad2d_clear, dev_status, stream):
     _check(lib().hgs_render_fwd(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
                                 ctypes.byref(cfg), ws, ws_bytes, image, final_T, n_contrib, vis, vis_words,
-                                dev_status, stream), "hgs_render_fwd")
+                                grad2d_clear, dev_status, stream), "hgs_render_fwd")
 
 
 def hgs_rasterize_bwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, final_T,
-                      n_contrib, vis, vis_words, dL_dimage, grad2d, dev_status, stream):
+                      n_contrib, vis, vis_words, dL_dimage, grad2d, grad2d_cleared, dev_status, stream):
     _check(lib().hgs_rasterize_bwd(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
                                    ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, vis, vis_words, dL_dimage,
-                                   grad2d, dev_status, stream), "hgs_rasterize_bwd")
+                                   grad2d, int(grad2d_cleared), dev_status, stream), "hgs_rasterize_bwd")
 
 
 def hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, fp64_list, dev_status, stream):

@@ -96,6 +96,7 @@ class Rasterizer:
         self.final_T = torch.empty(self.total_pixels, dtype=f32, device=dev)
         self.n_contrib = torch.empty(self.total_pixels, dtype=i32, device=dev)
         self.grad2d = torch.empty((vn, 12), dtype=f32, device=dev)
+        self._grad2d_cleared = False
         rws = H.hgs_render_workspace_size(self.cams_host, self.n_views, self.cfg, self.n)
         self.render_ws = torch.empty(max(rws, 16), dtype=torch.uint8, device=dev)
         self.capacity = 0
@@ -142,16 +143,22 @@ class Rasterizer:
         elif (image.numel() != self.image.numel() or image.dtype != self.image.dtype
               or image.device != self.image.device or not image.is_contiguous()):
             raise ValueError("image buffer must match the rasterizer's image (size, dtype, device, contiguous)")
+        # the kernel also clears grad2d for the backward that follows it on the stream
         H.hgs_render_fwd(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                          _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
                          _vp(image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
-                         _vp(self.status), self._stream())
+                         _vp(self.grad2d), _vp(self.status), self._stream())
+        self._grad2d_cleared = True
 
     def rasterize_bwd(self, dL_dimage: torch.Tensor):
+        # grad2d is already zero when the last call on it was render_fwd (which cleared it);
+        # a second backward after one forward clears it again
+        cleared, self._grad2d_cleared = self._grad2d_cleared, False
         H.hgs_rasterize_bwd(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                             _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws),
                             self.render_ws.numel(), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis),
-                            self.vis.numel(), _vp(dL_dimage), _vp(self.grad2d), _vp(self.status), self._stream())
+                            self.vis.numel(), _vp(dL_dimage), _vp(self.grad2d), cleared, _vp(self.status),
+                            self._stream())
 
     def project_bwd(self, g: Gaussians, out: Gaussians):
         H.hgs_project_bwd(g.c_struct(), self.cams_host, _vp(self.cams_dev), self.n_views, self.cfg,
@@ -172,6 +179,7 @@ class Rasterizer:
     def stats(self, dL_dimage: torch.Tensor) -> dict:
         """Work counters of one forward + backward compositing pass (hgs_render_stats)."""
         cnt = torch.zeros(8, dtype=torch.int64, device=self.device)
+        self._grad2d_cleared = False          # its backward leaves gradients in grad2d
         H.hgs_render_stats(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                            _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
                            _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),

@@ -16,7 +16,7 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, name), name
     for required in ("hgs_project", "hgs_bin", "hgs_render_fwd", "hgs_render_bwd"):
         assert required in names
-    assert H.hgs_version() == 1
+    assert H.hgs_version() == 2
     assert H.hgs_status_string(H.HGS_ERR_INVALID) == "invalid argument"
 
 

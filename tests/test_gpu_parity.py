@@ -9,6 +9,8 @@ of the tensor's largest entry) of the FP64 adjoint, with the upstream gradient
 zeroed on the exempt pixels, except at most 0.1% of entries, each within 1e-2
 and on a splat with a marked decision.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -261,3 +263,49 @@ def test_forward_into_a_caller_buffer(cuda_ok):
     assert torch.equal(buf, r.image)
     with pytest.raises(ValueError):
         r.render_fwd(torch.empty(r.image.numel() - 1, device=r.image.device))
+
+
+def test_forward_clears_the_backward_gradient_buffer(cuda_ok):
+    """render_fwd clears grad2d (grad2d_clear) and the backward after it skips its own
+    clearing; a second backward after the same forward clears it again.  All three
+    give the gradients of a backward that clears grad2d itself, whatever grad2d held."""
+    import torch
+    from paper_2406_02720_b300 import hgs as H
+    rng = np.random.default_rng(45)
+    sc = scenes.scene_uniform(rng, 1500, [-1.5, -1.0, 2.5], [1.5, 1.0, 6.0], -3.2, 0.6, 1.5, 1)
+    cams = [scenes.identity_camera(136, 88, 80.0)]
+    out = gpu_render(sc, cams)
+    r = out["rast"]
+    dL = torch.from_numpy(np.asarray(scenes.upstream_grad(46, cams)[0], np.float32).reshape(-1)).cuda()
+
+    def backward(clear_in_forward):
+        r.grad2d.fill_(7.0)                       # stale contents
+        r.clear_status()
+        if clear_in_forward:
+            r.render_fwd()
+            r.rasterize_bwd(dL)
+        else:
+            r.render_fwd()
+            r.grad2d.fill_(7.0)
+            H.hgs_rasterize_bwd(r.proj_struct(), r.n, ctypes.c_void_p(r.ids.data_ptr()),
+                                ctypes.c_void_p(r.ranges.data_ptr()), r.cams_host,
+                                ctypes.c_void_p(r.cams_dev.data_ptr()), r.n_views, r.cfg,
+                                ctypes.c_void_p(r.render_ws.data_ptr()), r.render_ws.numel(),
+                                ctypes.c_void_p(r.final_T.data_ptr()), ctypes.c_void_p(r.n_contrib.data_ptr()),
+                                ctypes.c_void_p(r.vis.data_ptr()), r.vis.numel(),
+                                ctypes.c_void_p(dL.data_ptr()), ctypes.c_void_p(r.grad2d.data_ptr()), 0,
+                                ctypes.c_void_p(r.status.data_ptr()),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert r.read_status() == 0
+        return r.grad2d.cpu().numpy().copy()
+
+    ref = backward(False)
+    got = backward(True)
+    r.grad2d.fill_(7.0)
+    r.rasterize_bwd(dL)                           # second backward after the same forward
+    assert r.read_status() == 0
+    again = r.grad2d.cpu().numpy()
+    scale = np.abs(ref).max(axis=0) + 1e-30
+    for g in (got, again):
+        np.testing.assert_allclose(g / scale, ref / scale, rtol=0, atol=1e-6)
+    assert np.count_nonzero(ref) > 1000
