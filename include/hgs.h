@@ -285,7 +285,7 @@ hgs_status hgs_bin_static(const hgs_proj *proj, int n, const hgs_camera *cams_ho
  * grad2d_clear (optional, [n_views*n, 12] floats, 16-B aligned; NULL: none): a
  * buffer the kernel sets to zero while it composites (its memory traffic is
  * light, so the stores cost it little), for a following hgs_rasterize_bwd given
- * grad2d_cleared = 1, which then skips clearing grad2d itself. */
+ * from_forward = 1, which then skips clearing grad2d itself. */
 hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
                           const uint32_t *ranges, const hgs_camera *cams_host,
                           const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
@@ -301,10 +301,13 @@ hgs_status hgs_render_fwd(const hgs_proj *proj, int n, const uint32_t *ids,
  * gradient of every (view, splat):
  *   grad2d [n_views*n, 12] (16-B aligned): d mu_x, d mu_y, d A, d B, d C,
  *          d w'_x, d w'_y, d alpha1, d alpha2, d r, d g, d b.
- * The call zeroes grad2d first, unless grad2d_cleared is non-zero: the caller
- * then vouches that grad2d is all zeros on entry (an hgs_render_fwd given it as
- * grad2d_clear, ordered before this call on the stream, with nothing written to
- * it in between).  Gradients through the 0.99 clamp, through
+ * The call zeroes grad2d first and builds its tile queue in ws, unless
+ * from_forward is non-zero: the caller then vouches that this call follows, on
+ * the same stream, the hgs_render_fwd it differentiates, called with the same
+ * proj, ranges, cameras, config and ws and with grad2d as its grad2d_clear, and
+ * that nothing has used ws or written grad2d in between (a second backward of
+ * the same forward passes 0).  grad2d is then already zero and the forward's
+ * tile queue is reused.  Gradients through the 0.99 clamp, through
  * skipped or terminated splats and through P of a degenerate plane are 0.
  * final_T, n_contrib and vis are the outputs of the hgs_render_fwd being
  * differentiated (same inputs, tile shape and batch): each 8x4 pixel block visits
@@ -318,7 +321,7 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids,
                              const hgs_camera *cams_dev, int n_views, const hgs_config *cfg,
                              void *ws, size_t ws_bytes, const float *final_T,
                              const uint32_t *n_contrib, const uint32_t *vis, size_t vis_words,
-                             const float *dL_dimage, float *grad2d, int grad2d_cleared,
+                             const float *dL_dimage, float *grad2d, int from_forward,
                              int *dev_status, void *stream);
 
 /* ---- A8: projection backward ------------------------------------------------ */

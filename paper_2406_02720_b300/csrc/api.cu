@@ -207,7 +207,7 @@ static hgs_status render_common(const hgs_proj *proj, int n, const uint32_t *ids
     p->vis_words = 0;
     p->clear = nullptr;
     p->clear_n4 = 0;
-    p->grad2d_cleared = false;
+    p->from_forward = false;
     p->dL_dimage = nullptr;
     p->grad2d = nullptr;
     p->status = nullptr;
@@ -242,7 +242,7 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, c
                              const hgs_camera *cams_host, const hgs_camera *cams_dev, int n_views,
                              const hgs_config *cfg, void *ws, size_t ws_bytes, const float *final_T,
                              const uint32_t *n_contrib, const uint32_t *vis, size_t vis_words,
-                             const float *dL_dimage, float *grad2d, int grad2d_cleared, int *dev_status,
+                             const float *dL_dimage, float *grad2d, int from_forward, int *dev_status,
                              void *stream) {
     RenderLaunch p;
     hgs_status st = render_common(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, &p);
@@ -255,7 +255,7 @@ hgs_status hgs_rasterize_bwd(const hgs_proj *proj, int n, const uint32_t *ids, c
     p.vis_words = vis_words;
     p.dL_dimage = dL_dimage;
     p.grad2d = grad2d;
-    p.grad2d_cleared = grad2d_cleared != 0;
+    p.from_forward = from_forward != 0;
     p.status = dev_status;
     return cuda_status(launch_render_bwd(p, static_cast<cudaStream_t>(stream)));
 }

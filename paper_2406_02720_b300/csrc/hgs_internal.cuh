@@ -109,7 +109,7 @@ struct RenderLaunch {
     size_t vis_words;
     float4 *clear;                  // forward: zeroed by the kernel (the backward's grad2d), or null
     size_t clear_n4;                // its length in float4
-    bool grad2d_cleared;            // backward: grad2d is already zero (no clearing)
+    bool from_forward;              // backward: follows its forward (grad2d cleared, queue built)
     // backward
     const float *dL_dimage;
     float *grad2d;

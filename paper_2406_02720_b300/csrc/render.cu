@@ -1054,7 +1054,10 @@ cudaError_t dispatch_batch(const RenderLaunch &p, cudaStream_t s) {
 template <bool FWD>
 cudaError_t dispatch(const RenderLaunch &p, cudaStream_t s) {
     if (p.vt.total_tiles == 0) return cudaSuccess;
-    if (p.cfg.persistent) {
+    // a backward that follows its forward on the same workspace reuses the forward's
+    // queue: the same order (a function of the ranges alone) and a backward counter the
+    // forward's build left at zero
+    if (p.cfg.persistent && !(!FWD && p.from_forward)) {
         cudaError_t e = prepare_queue(p, s);
         if (e != cudaSuccess) return e;
     }
@@ -1088,7 +1091,7 @@ size_t render_workspace_bytes(const ViewTable &vt, const hgs_config &cfg) {
 
 cudaError_t launch_render_fwd(const RenderLaunch &p, cudaStream_t s) { return dispatch<true>(p, s); }
 cudaError_t launch_render_bwd(const RenderLaunch &p, cudaStream_t s) {
-    if (!p.grad2d_cleared) {
+    if (!p.from_forward) {
         cudaError_t e = cudaMemsetAsync(p.grad2d, 0, sizeof(float) * 12 * (size_t)p.n * p.vt.n_views, s);
         if (e != cudaSuccess) return e;
     }

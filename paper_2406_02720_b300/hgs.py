@@ -184,10 +184,10 @@ def hgs_render_fwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, 
 
 
 def hgs_rasterize_bwd(proj, n, ids, ranges, cams_host, cams_dev, n_views, cfg, ws, ws_bytes, final_T,
-                      n_contrib, vis, vis_words, dL_dimage, grad2d, grad2d_cleared, dev_status, stream):
+                      n_contrib, vis, vis_words, dL_dimage, grad2d, from_forward, dev_status, stream):
     _check(lib().hgs_rasterize_bwd(ctypes.byref(proj), n, ids, ranges, cams_host, cams_dev, n_views,
                                    ctypes.byref(cfg), ws, ws_bytes, final_T, n_contrib, vis, vis_words, dL_dimage,
-                                   grad2d, int(grad2d_cleared), dev_status, stream), "hgs_rasterize_bwd")
+                                   grad2d, int(from_forward), dev_status, stream), "hgs_rasterize_bwd")
 
 
 def hgs_project_bwd(g, cams_host, cams_dev, n_views, cfg, grad2d, out, fp64_list, dev_status, stream):

@@ -96,7 +96,7 @@ class Rasterizer:
         self.final_T = torch.empty(self.total_pixels, dtype=f32, device=dev)
         self.n_contrib = torch.empty(self.total_pixels, dtype=i32, device=dev)
         self.grad2d = torch.empty((vn, 12), dtype=f32, device=dev)
-        self._grad2d_cleared = False
+        self._from_forward = False      # the last call on grad2d / render_ws was render_fwd
         rws = H.hgs_render_workspace_size(self.cams_host, self.n_views, self.cfg, self.n)
         self.render_ws = torch.empty(max(rws, 16), dtype=torch.uint8, device=dev)
         self.capacity = 0
@@ -148,16 +148,16 @@ class Rasterizer:
                          _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
                          _vp(image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
                          _vp(self.grad2d), _vp(self.status), self._stream())
-        self._grad2d_cleared = True
+        self._from_forward = True
 
     def rasterize_bwd(self, dL_dimage: torch.Tensor):
-        # grad2d is already zero when the last call on it was render_fwd (which cleared it);
-        # a second backward after one forward clears it again
-        cleared, self._grad2d_cleared = self._grad2d_cleared, False
+        # right after render_fwd, grad2d is already zero and the tile queue in render_ws is
+        # built; a second backward after one forward clears and builds them again
+        after_fwd, self._from_forward = self._from_forward, False
         H.hgs_rasterize_bwd(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                             _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws),
                             self.render_ws.numel(), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis),
-                            self.vis.numel(), _vp(dL_dimage), _vp(self.grad2d), cleared, _vp(self.status),
+                            self.vis.numel(), _vp(dL_dimage), _vp(self.grad2d), after_fwd, _vp(self.status),
                             self._stream())
 
     def project_bwd(self, g: Gaussians, out: Gaussians):
@@ -179,7 +179,7 @@ class Rasterizer:
     def stats(self, dL_dimage: torch.Tensor) -> dict:
         """Work counters of one forward + backward compositing pass (hgs_render_stats)."""
         cnt = torch.zeros(8, dtype=torch.int64, device=self.device)
-        self._grad2d_cleared = False          # its backward leaves gradients in grad2d
+        self._from_forward = False           # its own forward and backward reuse grad2d and render_ws
         H.hgs_render_stats(self.proj_struct(), self.n, _vp(self.ids), _vp(self.ranges), self.cams_host,
                            _vp(self.cams_dev), self.n_views, self.cfg, _vp(self.render_ws), self.render_ws.numel(),
                            _vp(self.image), _vp(self.final_T), _vp(self.n_contrib), _vp(self.vis), self.vis.numel(),
