@@ -328,11 +328,11 @@ def launches_per_step(total_tiles, persistent=False):
     """Kernels of one fwd+bwd step: k_project + k_project_fp64; binning =
     k_depth_keys, 3 per radix pass (k_upsweep, k_digit_scan, k_downsweep; all four
     depth passes are launched, those past the keys' range return at once),
-    k_scan_reduce, k_chunk_scan, k_duplicate, k_ranges; k_render_fwd and k_render_bwd,
-    each after k_queue_count + k_queue_fill when persistent; k_project_bwd +
-    k_project_bwd_fp64."""
+    k_scan_reduce, k_chunk_scan, k_duplicate, k_ranges; k_render_fwd, after
+    k_queue_count + k_queue_fill when persistent, and k_render_bwd (which reuses the
+    forward's queue); k_project_bwd + k_project_bwd_fp64."""
     dp, tp = n_sort_passes(total_tiles)
-    return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + 2 * (3 if persistent else 1) + 2
+    return 2 + (1 + 3 * dp + 3 + 3 * tp + 1) + (3 if persistent else 1) + 1 + 2
 
 
 def alg_bytes(n, n_pairs, total_tiles, depth_passes=4, views=1, drawn=None):

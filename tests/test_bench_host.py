@@ -53,8 +53,8 @@ def test_launch_and_pass_accounting():
     assert bench.n_sort_passes(257) == (4, 2)
     # project 2 + binning (1 + 3*4 + 3 + 3*2 + 1) + fwd + bwd + project_bwd 2
     assert bench.launches_per_step(8160, persistent=False) == 29
-    # + queue count and fill before each compositing kernel
-    assert bench.launches_per_step(8160, persistent=True) == 33
+    # + queue count and fill before the forward (the backward reuses its queue)
+    assert bench.launches_per_step(8160, persistent=True) == 31
 
 
 def test_depth_sort_passes():
